@@ -1,0 +1,305 @@
+"""FP64 CPU oracle of the spherical 2D-Gaussian rasterizer (Splat-LOAM, arXiv 2503.17491).
+
+TEST INFRASTRUCTURE ONLY: imported by ``tests/``, by ``__graft_entry__.smoke()`` and by the
+CPU-baseline leg of ``bench.py``.  The product path never imports it.
+
+This module is a ctypes wrapper around ``splat_oracle.c`` (plain C, FP64 render and gradient,
+plus its own implementation of the binary32 binning contract).  It shares no code with the CUDA
+library.  Every function takes and returns numpy arrays.
+
+Parity status per function (what pins it is in ``tests/test_oracle_*.py``):
+  render / render_backward : pinned (closed form, invariants, finite differences, brute force)
+  project_contract / bin   : pinned (brute-force coverage, wrap/pole/behind cases, series bounds)
+  loss / adam              : pinned (hand-computed values, textbook Adam recurrence)
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "splat_oracle.c")
+_LIB_DIR = os.path.join(_HERE, "_build")
+_LIB = os.path.join(_LIB_DIR, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+CFLAGS = ["-O2", "-std=gnu11", "-fPIC", "-shared", "-fopenmp", "-ffp-contract=off",
+          "-fno-fast-math"]
+
+
+def build(force: bool = False) -> str:
+    """Compile splat_oracle.c into _build/liboracle.so (gcc, no contraction of a*b+c)."""
+    os.makedirs(_LIB_DIR, exist_ok=True)
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", *CFLAGS, "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+_P = ctypes.c_void_p
+_I64 = ctypes.c_int64
+_I = ctypes.c_int
+_D = ctypes.c_double
+_F = ctypes.c_float
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            lib = ctypes.CDLL(build())
+            lib.or_version.restype = _I
+            lib.or_pose_inverse.argtypes = [_P, _P, _P]
+            lib.or_contract_atan2f.argtypes = [_F, _F]
+            lib.or_contract_atan2f.restype = _F
+            lib.or_contract_expf.argtypes = [_F]
+            lib.or_contract_expf.restype = _F
+            lib.or_project_contract.argtypes = [_I64, _P, _P, _P, _P, _I, _I, _F, _F, _I, _I,
+                                                _F, _I, _P, _P, _P, _P, _P, _P]
+            lib.or_bin.argtypes = [_I64, _P, _P, _P, _I, _I, _I, _I, _I64, _P, _P, _I64]
+            lib.or_bin.restype = _I64
+            lib.or_tile_ranges.argtypes = [_I64, _P, _I64, _I64, _P, _P]
+            lib.or_sort_order.argtypes = [_I64, _P, _P]
+            lib.or_render.argtypes = [_I64, _P, _P, _P, _P, _P, _P, _I64, _P, _P, _P, _P, _I, _I,
+                                      _D, _D, _I, _I, _P, _P, _P, _I64, _P, _P, _P, _P, _P, _P,
+                                      _I]
+            lib.or_render_backward.argtypes = [_I64, _P, _P, _P, _P, _P, _P, _I64, _P, _P, _P, _P,
+                                               _I, _I, _D, _D, _I, _I, _P, _P, _I64, _P, _P, _P,
+                                               _P, _P, _P, _P, _P, _P, _P, _I]
+            lib.or_reach_pairs.argtypes = [_I64, _P, _P, _P, _P, _P, _I, _I, _D, _D, _P, _P, _P,
+                                           _I64]
+            lib.or_reach_pairs.restype = _I64
+            lib.or_loss.argtypes = [_I64, _P, _P, _P, _P, _P, _D, _D, _D, _P, _P, _P]
+            lib.or_loss.restype = _D
+            lib.or_adam.argtypes = [_I64, _P, _P, _P, _P, _D, _D, _D, _D, _I]
+            _lib = lib
+    return _lib
+
+
+def _ptr(a):
+    return None if a is None else a.ctypes.data
+
+
+def _c(a, dtype):
+    return np.ascontiguousarray(a, dtype=dtype)
+
+
+# Default per-pixel cutoffs (3DGS conventions; the paper gives none): alpha_min, alpha_max,
+# t_min, sigma_cut.
+DEFAULT_CFG = (1.0 / 255.0, 0.99, 1e-4, 3.0)
+
+
+def pose_inverse(T_ws):
+    R = np.zeros(9)
+    t = np.zeros(3)
+    _load().or_pose_inverse(_ptr(_c(T_ws, np.float64)), _ptr(R), _ptr(t))
+    return R.reshape(3, 3), t
+
+
+def contract_atan2f(y, x) -> float:
+    return float(_load().or_contract_atan2f(float(np.float32(y)), float(np.float32(x))))
+
+
+def contract_expf(x) -> float:
+    return float(_load().or_contract_expf(float(np.float32(x))))
+
+
+def project_contract(pos_logit, quat, log_scale, T_ws, rows, cols, elev_min, elev_max,
+                     tile_h=16, tile_w=16, sigma_cut=3.0, flip_normals=1):
+    """Binary32 contract for one view: kappa, flip (+1/-1), pixel rect (r0, r1, c0, nc),
+    tile rect (tr0, tr1, tc0, ntc), tile count, valid flag."""
+    pl = _c(pos_logit, np.float32)
+    q = _c(quat, np.float32)
+    ls = _c(log_scale, np.float32)
+    n = pl.shape[0]
+    kappa = np.zeros(n, np.float32)
+    flip = np.zeros(n, np.int8)
+    pix = np.zeros((n, 4), np.int32)
+    til = np.zeros((n, 4), np.int32)
+    cnt = np.zeros(n, np.int32)
+    valid = np.zeros(n, np.uint8)
+    _load().or_project_contract(n, _ptr(pl), _ptr(q), _ptr(ls), _ptr(_c(T_ws, np.float64)),
+                                rows, cols, float(np.float32(elev_min)),
+                                float(np.float32(elev_max)), tile_h, tile_w,
+                                float(np.float32(sigma_cut)), int(flip_normals),
+                                _ptr(kappa), _ptr(flip), _ptr(pix), _ptr(til), _ptr(cnt),
+                                _ptr(valid))
+    return dict(kappa=kappa, flip=flip, pix_rect=pix, tile_rect=til, count=cnt, valid=valid)
+
+
+def bin_pairs(proj, rows, cols, tile_h=16, tile_w=16, tile_offset=0):
+    """Sorted (key, id) of every (tile, primitive) pair; key = (tile_offset + tile) << 32 |
+    bits(kappa)."""
+    cnt = proj["count"]
+    m = int(cnt.astype(np.int64).sum())
+    keys = np.zeros(max(m, 1), np.uint64)
+    ids = np.zeros(max(m, 1), np.uint32)
+    got = _load().or_bin(len(cnt), _ptr(proj["kappa"]), _ptr(proj["tile_rect"]), _ptr(cnt),
+                         rows, cols, tile_h, tile_w, tile_offset, _ptr(keys), _ptr(ids), m)
+    assert got == m
+    return keys[:m], ids[:m]
+
+
+def tile_ranges(keys, n_tiles, tile_offset=0):
+    keys = _c(keys, np.uint64)
+    start = np.zeros(n_tiles, np.int64)
+    end = np.zeros(n_tiles, np.int64)
+    _load().or_tile_ranges(len(keys), _ptr(keys), tile_offset, n_tiles, _ptr(start), _ptr(end))
+    return start, end
+
+
+def sort_order(kappa):
+    kappa = _c(kappa, np.float32)
+    order = np.zeros(len(kappa), np.int32)
+    _load().or_sort_order(len(kappa), _ptr(kappa), _ptr(order))
+    return order
+
+
+def split_params(pos_logit, quat, log_scale):
+    """FP32 parameter arrays -> exact FP64 copies (pos, logit, quat, log_scale)."""
+    pl = np.asarray(pos_logit, np.float64)
+    return (_c(pl[:, :3], np.float64), _c(pl[:, 3], np.float64), _c(quat, np.float64),
+            _c(log_scale, np.float64))
+
+
+class Culled:
+    """Per-tile lists of one view (culled mode): start, end per tile, primitive ids."""
+
+    def __init__(self, keys, ids, rows, cols, tile_h, tile_w):
+        n_tiles = -(-rows // tile_h) * -(-cols // tile_w)
+        self.start, self.end = tile_ranges(keys, n_tiles)
+        self.ids = _c(ids, np.int32)
+        self.tile_h, self.tile_w = tile_h, tile_w
+
+
+def render(params, flip, order, T_ws, rows, cols, elev_min, elev_max, cfg=DEFAULT_CFG,
+           band=None, culled: Culled | None = None, tile_h=16, tile_w=16, n_threads=0,
+           pixels=None):
+    """FP64 forward of one view.  params = (pos, logit, quat, log_scale) FP64 arrays;
+    flip = int8 +-1 per primitive; order = brute-mode composite order (ignored if culled).
+    pixels: optional (k,2) int array of (row, col) to render instead of the whole image.
+    Returns dict D (H,W), N (3,H,W), O, T (final transmittance), n_contrib, band flags
+    (shapes (k,), (3,k), ... when pixels is given)."""
+    pos, logit, quat, ls = [_c(a, np.float64) for a in params]
+    n = pos.shape[0]
+    px = None if pixels is None else _c(pixels, np.int32).reshape(-1, 2)
+    hw = rows * cols if px is None else len(px)
+    D = np.zeros(hw)
+    N = np.zeros(3 * hw)
+    O = np.zeros(hw)
+    T = np.zeros(hw)
+    nc = np.zeros(hw, np.int32)
+    bf = np.zeros(hw, np.uint8)
+    order = _c(order if order is not None else np.arange(n), np.int32)
+    cfg_a = np.asarray(cfg, np.float64)
+    band_a = None if band is None else np.asarray(band, np.float64)
+    if culled is not None:
+        ts, te, ti, th, tw = culled.start, culled.end, culled.ids, culled.tile_h, culled.tile_w
+    else:
+        ts = te = ti = None
+        th, tw = tile_h, tile_w
+    _load().or_render(n, _ptr(pos), _ptr(logit), _ptr(quat), _ptr(ls),
+                      _ptr(_c(flip, np.int8)), _ptr(order), len(order), _ptr(ts), _ptr(te),
+                      _ptr(ti), _ptr(_c(T_ws, np.float64)), rows, cols,
+                      float(elev_min), float(elev_max), th, tw, _ptr(cfg_a), _ptr(band_a),
+                      _ptr(px), 0 if px is None else len(px),
+                      _ptr(D), _ptr(N), _ptr(O), _ptr(T), _ptr(nc), _ptr(bf), n_threads)
+    shp = (rows, cols) if px is None else (len(px),)
+    return dict(D=D.reshape(shp), N=N.reshape((3,) + shp), O=O.reshape(shp), T=T.reshape(shp),
+                n_contrib=nc.reshape(shp), band=bf.reshape(shp))
+
+
+def render_backward(params, flip, order, T_ws, rows, cols, elev_min, elev_max, gD, gN, gO,
+                    cfg=DEFAULT_CFG, culled: Culled | None = None, tile_h=16, tile_w=16,
+                    n_threads=0, pixels=None):
+    """FP64 analytic gradient of L = sum gD*D + gN.N + gO*O (over the given pixels, or all).
+    Returns dict with g_pos (n,3), g_logit (n,), g_quat (n,4), g_log_scale (n,2),
+    g_b (n,9) = (b_a, b_b, b_c) in the sensor frame, g_n (n,3), g_o (n,)."""
+    px = None if pixels is None else _c(pixels, np.int32).reshape(-1, 2)
+    pos, logit, quat, ls = [_c(a, np.float64) for a in params]
+    n = pos.shape[0]
+    out = dict(g_pos=np.zeros((n, 3)), g_logit=np.zeros(n), g_quat=np.zeros((n, 4)),
+               g_log_scale=np.zeros((n, 2)), g_b=np.zeros((n, 9)), g_n=np.zeros((n, 3)),
+               g_o=np.zeros(n))
+    order = _c(order if order is not None else np.arange(n), np.int32)
+    if culled is not None:
+        ts, te, ti, th, tw = culled.start, culled.end, culled.ids, culled.tile_h, culled.tile_w
+    else:
+        ts = te = ti = None
+        th, tw = tile_h, tile_w
+    _load().or_render_backward(
+        n, _ptr(pos), _ptr(logit), _ptr(quat), _ptr(ls), _ptr(_c(flip, np.int8)), _ptr(order),
+        len(order), _ptr(ts), _ptr(te), _ptr(ti), _ptr(_c(T_ws, np.float64)), rows, cols,
+        float(elev_min), float(elev_max), th, tw, _ptr(np.asarray(cfg, np.float64)),
+        _ptr(px), 0 if px is None else len(px), _ptr(_c(gD, np.float64).ravel()), _ptr(_c(gN, np.float64).ravel()),
+        _ptr(_c(gO, np.float64).ravel()), _ptr(out["g_pos"]), _ptr(out["g_logit"]),
+        _ptr(out["g_quat"]), _ptr(out["g_log_scale"]), _ptr(out["g_b"]), _ptr(out["g_n"]),
+        _ptr(out["g_o"]), n_threads)
+    return out
+
+
+def reach_pairs(params, T_ws, rows, cols, elev_min, elev_max, cfg=DEFAULT_CFG,
+                cap=50_000_000):
+    """Brute force: every (pixel index, primitive) whose ray reaches the primitive, without
+    compositing (box test, hit in front, alpha >= alpha_min)."""
+    pos, logit, quat, ls = [_c(a, np.float64) for a in params]
+    n = pos.shape[0]
+    pix = np.zeros(cap, np.int64)
+    prim = np.zeros(cap, np.int32)
+    k = _load().or_reach_pairs(n, _ptr(pos), _ptr(logit), _ptr(quat), _ptr(ls),
+                               _ptr(_c(T_ws, np.float64)), rows, cols, float(elev_min),
+                               float(elev_max), _ptr(np.asarray(cfg, np.float64)), _ptr(pix),
+                               _ptr(prim), cap)
+    assert k <= cap
+    return pix[:k], prim[:k]
+
+
+def loss(D, N, O, Dt, Nt, lambda_n=1.0, lambda_o=0.0, o_eps=1e-6):
+    """(L, gD, gN, gO) over flattened pixels; N, Nt are (3, npx) planar."""
+    D = _c(D, np.float64).ravel()
+    npx = D.size
+    gD = np.zeros(npx)
+    gN = np.zeros(3 * npx)
+    gO = np.zeros(npx)
+    L = _load().or_loss(npx, _ptr(D), _ptr(_c(N, np.float64).ravel()),
+                        _ptr(_c(O, np.float64).ravel()), _ptr(_c(Dt, np.float64).ravel()),
+                        _ptr(_c(Nt, np.float64).ravel()), lambda_n, lambda_o, o_eps,
+                        _ptr(gD), _ptr(gN), _ptr(gO))
+    return L, gD, gN.reshape(3, npx), gO
+
+
+def adam(p, g, m, v, lr, b1=0.9, b2=0.999, eps=1e-15, step=1):
+    """In-place FP64 Adam on 1-D float64 arrays."""
+    for a in (p, m, v):
+        assert a.dtype == np.float64 and a.flags.c_contiguous
+    _load().or_adam(p.size, _ptr(p), _ptr(_c(g, np.float64)), _ptr(m), _ptr(v), lr, b1, b2,
+                    eps, int(step))
+
+
+def full_view(pos_logit, quat, log_scale, T_ws, rows, cols, elev_min, elev_max, *,
+              cfg=DEFAULT_CFG, band=None, tile_h=16, tile_w=16, mode="culled", flip_normals=1,
+              n_threads=0):
+    """Convenience: contract + binning + FP64 render of one view from FP32 inputs."""
+    proj = project_contract(pos_logit, quat, log_scale, T_ws, rows, cols, elev_min, elev_max,
+                            tile_h, tile_w, cfg[3], flip_normals)
+    params = split_params(pos_logit, quat, log_scale)
+    emin, emax = float(np.float32(elev_min)), float(np.float32(elev_max))
+    if mode == "culled":
+        keys, ids = bin_pairs(proj, rows, cols, tile_h, tile_w)
+        cul = Culled(keys, ids, rows, cols, tile_h, tile_w)
+        out = render(params, proj["flip"], None, T_ws, rows, cols, emin, emax, cfg, band,
+                     culled=cul, n_threads=n_threads)
+        out["keys"], out["ids"], out["culled"] = keys, ids, cul
+    else:
+        order = sort_order(proj["kappa"])
+        out = render(params, proj["flip"], order, T_ws, rows, cols, emin, emax, cfg, band,
+                     tile_h=tile_h, tile_w=tile_w, n_threads=n_threads)
+        out["order"] = order
+    out["proj"], out["params"] = proj, params
+    return out

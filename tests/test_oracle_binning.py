@@ -1,0 +1,181 @@
+"""Pins of the oracle's binary32 binning contract (Sec. 3.2.1 tiles and range sort, Sec. 3.2.3
+bounding box; Supp. B).
+
+* the series used for atan2 and exp stay within their error bounds;
+* brute force: every (pixel, primitive) pair whose ray reaches the primitive (box test, in front,
+  alpha >= alpha_min) lies in the primitive's pixel rectangle and in one of its tiles;
+* hand-built cases: the +-pi seam behind the sensor, a splat over the pole, the sensor inside
+  the 3-sigma box, an edge-on splat;
+* the sorted key list is consistent: sorted by (tile, kappa bits, id), each primitive listed once
+  per touched tile, tile ranges partition the list.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from paper_2503_17491_gb300 import scenes
+
+
+def test_contract_atan2_bound(oracle_mod):
+    rng = np.random.default_rng(0)
+    ys = np.concatenate([rng.normal(size=4000) * 10 ** rng.uniform(-3, 3, 4000),
+                         [0, 0, 1, -1, 1e-30, -1e-30, 3, -3]]).astype(np.float32)
+    xs = np.concatenate([rng.normal(size=4000) * 10 ** rng.uniform(-3, 3, 4000),
+                         [1, -1, 0, 0, -1, -1, 3, 3]]).astype(np.float32)
+    worst = 0.0
+    for y, x in zip(ys, xs):
+        if x == 0 and y == 0:
+            continue
+        worst = max(worst, abs(oracle_mod.contract_atan2f(y, x) - math.atan2(float(y), float(x))))
+    assert worst < 4e-7
+    assert oracle_mod.contract_atan2f(0.0, 1.0) == 0.0
+    assert oracle_mod.contract_atan2f(1.0, 0.0) == float(np.float32(math.pi / 2))
+    assert oracle_mod.contract_atan2f(0.0, -1.0) == float(np.float32(math.pi))
+    assert oracle_mod.contract_atan2f(-1e-30, -1.0) == -float(np.float32(math.pi))
+
+
+def test_contract_exp_bound(oracle_mod):
+    xs = np.linspace(-20, 10, 30001).astype(np.float32)
+    rel = max(abs(oracle_mod.contract_expf(x) / math.exp(float(x)) - 1) for x in xs[::7])
+    assert rel < 2e-7
+    assert oracle_mod.contract_expf(0.0) == 1.0
+    assert oracle_mod.contract_expf(1.0) == pytest.approx(math.e, rel=2e-7)
+
+
+def test_pose_inverse(oracle_mod):
+    T = scenes.random_pose(np.random.default_rng(1), 5.0, 40.0)
+    R, t = oracle_mod.pose_inverse(T)
+    Ti = np.eye(4)
+    Ti[:3, :3], Ti[:3, 3] = R, t
+    np.testing.assert_allclose(Ti @ T, np.eye(4), atol=1e-14)
+
+
+def _in_cyclic(x, start, count, period):
+    return ((x - start) % period) < count
+
+
+def _check_coverage(oracle_mod, pl, q, ls, v, th=16, tw=16, min_pairs=1):
+    proj = oracle_mod.project_contract(pl, q, ls, v.T_ws, v.rows, v.cols, v.elev_min,
+                                       v.elev_max, th, tw)
+    params = oracle_mod.split_params(pl, q, ls)
+    pix, prim = oracle_mod.reach_pairs(params, v.T_ws, v.rows, v.cols, v.elev_min, v.elev_max)
+    assert len(pix) >= min_pairs
+    r, c = pix // v.cols, pix % v.cols
+    pr = proj["pix_rect"][prim]
+    tr = proj["tile_rect"][prim]
+    TC = -(-v.cols // tw)
+    assert np.all(proj["count"][prim] > 0)
+    assert np.all((r >= pr[:, 0]) & (r <= pr[:, 1]))
+    assert np.all(_in_cyclic(c, pr[:, 2], pr[:, 3], v.cols))
+    assert np.all((r // th >= tr[:, 0]) & (r // th <= tr[:, 1]))
+    assert np.all(_in_cyclic(c // tw, tr[:, 2], tr[:, 3], TC))
+    return proj, pix, prim
+
+
+def test_coverage_workload0(oracle_mod):
+    s = scenes.workload(0)
+    v = s.views[0]
+    proj, pix, prim = _check_coverage(oracle_mod, s.pos_logit, s.quat, s.log_scale, v,
+                                      min_pairs=1000)
+    # and the box is not wildly loose: the pixel rectangles hold at most ~6x the reached pixels
+    area = (proj["pix_rect"][:, 1] - proj["pix_rect"][:, 0] + 1) * proj["pix_rect"][:, 3]
+    area = np.where(proj["count"] > 0, area, 0).sum()
+    assert area < 6 * len(pix)
+
+
+@pytest.mark.parametrize("seed", range(4))
+@pytest.mark.parametrize("tile", [(16, 16), (8, 32), (32, 8), (4, 64)])
+def test_coverage_tiny_random(oracle_mod, seed, tile):
+    s = scenes.tiny_scene(60, seed, rows=24, cols=200, fov_deg=35, dist=(0.6, 9.0),
+                          spread=2.0, log_scale=(-3.0, -0.5))
+    s.views[0].T_ws = scenes.random_pose(np.random.default_rng(seed + 10), 0.2, 30.0)
+    _check_coverage(oracle_mod, s.pos_logit, s.quat, s.log_scale, s.views[0], *tile,
+                    min_pairs=50)
+
+
+def _single(mu, normal_q, s, o=0.9):
+    pl = np.array([[*mu, math.log(o / (1 - o))]], np.float32)
+    q = np.array([normal_q], np.float32)
+    ls = np.array([[math.log(s[0]), math.log(s[1])]], np.float32)
+    return pl, q, ls
+
+
+def test_seam_behind_sensor(oracle_mod):
+    """A splat straddling azimuth +-pi (behind the sensor): its columns wrap from W-1 to 0."""
+    v = scenes.View(np.eye(4), 32, 512, scenes.deg(-15), scenes.deg(15))
+    # at x = -4 facing the sensor: t_a = y, t_b = z, t_n = x (quaternion of 120 deg about 1,1,1)
+    pl, q, ls = _single((-4.0, 0.05, 0.0), (0.5, 0.5, 0.5, 0.5), (0.3, 0.3))
+    proj, pix, prim = _check_coverage(oracle_mod, pl, q, ls, v, min_pairs=20)
+    c = pix % v.cols
+    assert c.min() == 0 and c.max() == v.cols - 1       # both image edges are reached
+    c0, nc = proj["pix_rect"][0, 2], proj["pix_rect"][0, 3]
+    assert c0 + nc > v.cols                              # the rectangle wraps
+    assert proj["tile_rect"][0, 2] + proj["tile_rect"][0, 3] > v.cols // 16
+    out = oracle_mod.full_view(pl, q, ls, v.T_ws, v.rows, v.cols, v.elev_min, v.elev_max)
+    ref = oracle_mod.full_view(pl, q, ls, v.T_ws, v.rows, v.cols, v.elev_min, v.elev_max,
+                               mode="brute")
+    np.testing.assert_array_equal(out["D"], ref["D"])
+
+
+def test_splat_over_the_pole(oracle_mod):
+    """A horizontal splat above the sensor covers every azimuth of the top rows."""
+    v = scenes.View(np.eye(4), 48, 256, scenes.deg(-80), scenes.deg(80))
+    pl, q, ls = _single((0.3, -0.2, 2.0), (1.0, 0.0, 0.0, 0.0), (0.37, 0.3))
+    proj, pix, prim = _check_coverage(oracle_mod, pl, q, ls, v, min_pairs=100)
+    assert proj["pix_rect"][0, 3] == v.cols and proj["pix_rect"][0, 0] == 0
+    assert len(np.unique(pix % v.cols)) == v.cols
+
+
+def test_sensor_inside_box(oracle_mod):
+    """The sensor 0.1 m off the plane with its foot inside the 3-sigma box.  A vertical plane:
+    the reached columns span nearly 180 degrees and stay inside the box.  A horizontal plane
+    just below the sensor: every column."""
+    v = scenes.View(np.eye(4), 32, 256, scenes.deg(-40), scenes.deg(40))
+    pl, q, ls = _single((0.1, 0.2, -0.1), (0.5, 0.5, 0.5, 0.5), (0.35, 0.35))
+    proj, pix, prim = _check_coverage(oracle_mod, pl, q, ls, v, min_pairs=100)
+    assert len(np.unique(pix % v.cols)) > 100
+    pl, q, ls = _single((0.05, -0.1, -0.1), (1.0, 0.0, 0.0, 0.0), (0.35, 0.35))
+    proj, pix, prim = _check_coverage(oracle_mod, pl, q, ls, v, min_pairs=100)
+    assert proj["pix_rect"][0, 3] == v.cols
+    assert len(np.unique(pix % v.cols)) == v.cols
+
+
+def test_edge_on_splat(oracle_mod):
+    """A splat whose plane nearly contains the sensor: reached pixels form a thin sliver and
+    stay inside the box."""
+    v = scenes.View(np.eye(4), 64, 1024, scenes.deg(-20), scenes.deg(20))
+    # plane y = 0.05 (normal +y): t_a = x, t_b = z -> rotation of -90 deg about x;
+    # rays at azimuth 0.47-0.73 deg graze it (one column of a 1024-wide image)
+    c, s_ = math.cos(-math.pi / 4), math.sin(-math.pi / 4)
+    pl, q, ls = _single((5.0, 0.05, 0.0), (c, s_, 0.0, 0.0), (0.37, 0.37))
+    _check_coverage(oracle_mod, pl, q, ls, v, min_pairs=1)
+
+
+def test_sorted_keys_and_ranges(oracle_mod):
+    s = scenes.workload(0)
+    v = s.views[0]
+    th, tw = 16, 16
+    proj = oracle_mod.project_contract(s.pos_logit, s.quat, s.log_scale, v.T_ws, v.rows, v.cols,
+                                       v.elev_min, v.elev_max, th, tw)
+    keys, ids = oracle_mod.bin_pairs(proj, v.rows, v.cols, th, tw)
+    assert len(keys) == proj["count"].sum()
+    # sorted by (key, id); key = tile << 32 | bits(kappa)
+    k2 = keys.astype(object) * (1 << 32) + ids.astype(object)
+    assert all(k2[i] < k2[i + 1] for i in range(len(k2) - 1))
+    np.testing.assert_array_equal((keys & 0xFFFFFFFF).astype(np.uint32),
+                                  proj["kappa"][ids].view(np.uint32))
+    # each primitive appears exactly once per tile of its rectangle
+    TC = -(-v.cols // tw)
+    tiles = (keys >> 32).astype(np.int64)
+    for i in np.unique(ids)[:200]:
+        t = np.sort(tiles[ids == i])
+        tr = proj["tile_rect"][i]
+        want = sorted(rr * TC + (tr[2] + k) % TC for rr in range(tr[0], tr[1] + 1)
+                      for k in range(tr[3]))
+        np.testing.assert_array_equal(t, want)
+    n_tiles = -(-v.rows // th) * TC
+    start, end = oracle_mod.tile_ranges(keys, n_tiles)
+    nonempty = end > start
+    assert (end - start)[nonempty].sum() == len(keys)
+    assert np.all(tiles[start[nonempty]] == np.nonzero(nonempty)[0])

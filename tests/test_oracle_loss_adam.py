@@ -1,0 +1,48 @@
+"""Pins of the oracle's loss (Eqs. loss_range, loss_normal, loss_opacity over the valid mask M_v)
+and Adam step, against hand-computed values and Adam's known closed-form behaviour."""
+import math
+
+import numpy as np
+import pytest
+
+
+def test_loss_hand_values(oracle_mod):
+    # 4 pixels; the last has target range 0 (ray drop: outside M_v)
+    D = np.array([2.0, 5.0, 1.0, 7.0])
+    Dt = np.array([1.5, 5.0, 3.0, 0.0])
+    N = np.array([[0.0, 1.0, 0.6, 1.0], [0.0, 0.0, 0.8, 0.0], [-1.0, 0.0, 0.0, 0.0]])
+    Nt = np.array([[0.0, 0.0, 0.6, 1.0], [0.0, 1.0, 0.8, 0.0], [-1.0, 0.0, 0.0, 0.0]])
+    O = np.array([0.5, 1.0, 0.25, 0.9])
+    L, gD, gN, gO = oracle_mod.loss(D, N, O, Dt, Nt, lambda_n=0.5, lambda_o=0.1)
+    # L_d = 0.5 + 0 + 2 ; L_n = 0.5 * ((1-1) + (1-0) + (1-1)) ; L_o = 0.1 * (ln 2 + 0 + ln 4)
+    want = 2.5 + 0.5 * 1.0 + 0.1 * (math.log(2) + math.log(4))
+    assert L == pytest.approx(want, rel=1e-14)
+    np.testing.assert_array_equal(gD, [1.0, 0.0, -1.0, 0.0])
+    np.testing.assert_allclose(gN[:, :3], -0.5 * Nt[:, :3])
+    assert np.all(gN[:, 3] == 0)
+    np.testing.assert_allclose(gO, [-0.1 / 0.5, -0.1, -0.1 / 0.25, 0.0])
+
+
+def test_adam_first_step_is_lr_times_sign(oracle_mod):
+    """With bias correction, Adam's first update is -lr * g / |g| (m_hat = g, v_hat = g^2)."""
+    rng = np.random.default_rng(0)
+    p = rng.normal(size=100)
+    g = rng.normal(size=100) * 10 ** rng.uniform(-4, 4, 100)
+    p0 = p.copy()
+    m = np.zeros(100)
+    v = np.zeros(100)
+    oracle_mod.adam(p, g, m, v, lr=1e-2, eps=1e-15, step=1)
+    np.testing.assert_allclose(p - p0, -1e-2 * np.sign(g), rtol=1e-9)
+
+
+def test_adam_constant_gradient(oracle_mod):
+    """A constant gradient keeps m_hat = g and v_hat = g^2 at every step: each update is
+    -lr * sign(g) again."""
+    p = np.array([1.0, -2.0, 3.0])
+    g = np.array([0.5, -3.0, 1e-3])
+    m = np.zeros(3)
+    v = np.zeros(3)
+    for t in range(1, 6):
+        before = p.copy()
+        oracle_mod.adam(p, g, m, v, lr=0.1, b1=0.9, b2=0.99, eps=1e-15, step=t)
+        np.testing.assert_allclose(p - before, -0.1 * np.sign(g), rtol=1e-9)
