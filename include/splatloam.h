@@ -1,0 +1,261 @@
+/*
+ * splatloam.h -- C ABI of libsplatloam, a GB300 (sm_103a) differentiable rasterizer of 2D
+ * Gaussian primitives into LiDAR spherical range images, after Splat-LOAM (arXiv 2503.17491).
+ *
+ * What the library computes (the paper's statement of the problem):
+ *   render   : primitives {o, mu, R = (t_alpha, t_beta, t_n), s} (Sec. 3.2, Eq. world_T_splat),
+ *              a sensor pose and LiDAR intrinsics -> per-pixel range D, normal N and accumulated
+ *              opacity O by front-to-back alpha blending over per-tile lists sorted by range
+ *              (Sec. 3.2.1, Eqs. ab_depth, ab_normal, ab_opacity), each ray intersected with each
+ *              splat as two planes (Sec. 3.2.2, Eq. planes_to_splat; Supp. D.1), with a spherical
+ *              bounding box that handles the +-pi azimuth seam (Sec. 3.2.3, Supp. B).
+ *   backward : per-pixel dL/dD, dL/dN, dL/dO -> dL/d(every primitive parameter) (Supp. D.2, with
+ *              the dL/dO channel and the chain rule through the parametrisation below).
+ *   loss     : L_d + lambda_n L_n (+ lambda_o L_o) over valid pixels (Sec. 3.3.2, Eqs.
+ *              loss_range, loss_normal, loss_opacity), with its per-pixel gradients.
+ *   adam     : one Adam step of all primitive parameters (the paper does not name its
+ *              optimiser; Adam is used here).
+ *
+ * Conventions (every call):
+ *   - Primitive parameters, one row per primitive, float32, device memory owned by the caller:
+ *       pos_logit  n x 4 : (mu_x, mu_y, mu_z, logit(o))       o = 1 / (1 + exp(-logit))
+ *       quat_wxyz  n x 4 : (w, x, y, z), any nonzero length   R = R(q / |q|), columns t_a, t_b, t_n
+ *       log_scale  n x 2 : (log s_alpha, log s_beta)          s = exp(log_scale)
+ *   - Poses: T_world_sensor is a host array of 16 doubles, row-major 4x4, sensor -> world, a
+ *     rigid transform.  The library inverts it in FP64 to get T^c_w (Sec. 3.2.2).
+ *   - Sensor frame: x forward, y left, z up (Sec. 3.1).  Pixel (r, c) of a rows x cols image
+ *     looks along azimuth pi - 2 pi (c + 1/2) / cols and elevation
+ *     elev_max - r (elev_max - elev_min) / (rows - 1); column cols/2 - 1/2 looks along +x.
+ *   - Images: all registered views are packed one after the other.  View v occupies pixels
+ *     [pixel_offset(v), pixel_offset(v) + rows_v * cols_v) of a buffer of P = sum rows_v cols_v
+ *     pixels, row-major inside the view.  depth and alpha are float32[P]; normal is float32[3][P]
+ *     (three planes of P pixels: x, y, z).  N is in the sensor frame of its view; D is the blended
+ *     range (not divided by O).
+ *   - Every compute call is asynchronous and stream-ordered on `stream` (a cudaStream_t, or NULL
+ *     for the legacy default stream), never synchronises the host and never allocates: all
+ *     workspace is owned by the context and sized at creation, so a sequence of calls can be
+ *     captured into a CUDA graph.  Exceptions: splat_ctx_create/destroy, splat_set_views (which
+ *     uploads view tables synchronously) and splat_get_status/splat_get_stats/splat_debug_copy
+ *     (which synchronise).
+ *   - Return codes: SPLAT_OK, or an error code (errors never cross the ABI as exceptions).
+ *     Errors found on the device (capacity overflow, non-finite input) are recorded in a status
+ *     word and reported by splat_get_status after the stream is synchronised.
+ *   - A context is not thread-safe; use one per host thread / stream.
+ */
+#ifndef SPLATLOAM_H
+#define SPLATLOAM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define SPLAT_API __attribute__((visibility("default")))
+
+typedef struct splat_ctx splat_ctx;
+
+/* Return codes. */
+enum {
+    SPLAT_OK = 0,
+    SPLAT_ERR_INVALID_ARG = 1,  /* null pointer, bad size, non-finite pose, rows/cols < 2, ... */
+    SPLAT_ERR_CUDA = 2,         /* a CUDA runtime call failed; see splat_last_cuda_error       */
+    SPLAT_ERR_CAPACITY = 3,     /* more (tile, primitive) pairs than max_pairs: outputs invalid */
+    SPLAT_ERR_TIMEOUT = 4,      /* a bounded device wait gave up                               */
+    SPLAT_ERR_NONFINITE = 5,    /* a primitive had a non-finite value or a zero quaternion     */
+    SPLAT_ERR_STATE = 6,        /* call order violated (e.g. backward before any render)       */
+    SPLAT_ERR_UNSUPPORTED = 7   /* configuration not built into this library (tile shape)      */
+};
+
+/* Bits of the device status word (splat_get_status). */
+enum {
+    SPLAT_STATUS_CAPACITY = 1u,
+    SPLAT_STATUS_NONFINITE = 2u,
+    SPLAT_STATUS_TIMEOUT = 4u
+};
+
+/* LiDAR intrinsics of one view: image size and elevation range in radians
+ * (elev_min < elev_max, both inside (-pi/2, pi/2)); azimuth always spans 360 degrees. */
+typedef struct {
+    int32_t rows, cols;
+    float elev_min, elev_max;
+} splat_lidar_intrinsics;
+
+/* The primitives (device pointers, caller-owned; layout in the header comment). */
+typedef struct {
+    const float *pos_logit;   /* n x 4 */
+    const float *quat_wxyz;   /* n x 4 */
+    const float *log_scale;   /* n x 2 */
+    int64_t n;
+} splat_gaussians;
+
+/* Rasterizer settings.  The paper gives no cutoffs; the defaults are the 3DGS conventions it
+ * builds on (Sec. 3.2.1): alpha_min 1/255, alpha_max 0.99, t_min 1e-4, plus the 3-sigma box of
+ * Sec. 3.2.3 (sigma_cut 3).  Tiles are tile_h x tile_w pixels with tile_h * tile_w == 256;
+ * built shapes: 16x16 (the paper's), 8x32, 32x8, 4x64.  flip_normals = 1 turns each normal
+ * towards the sensor.  work_cap is reserved (must be 0). */
+typedef struct {
+    float alpha_min, alpha_max, t_min, sigma_cut;
+    int32_t tile_h, tile_w, work_cap, flip_normals;
+} splat_render_config;
+
+/* Workspace limits fixed at creation.  max_pairs bounds the number of (tile, primitive) pairs
+ * of one render call summed over views; max_tiles = 0 derives a bound from max_pixels. */
+typedef struct {
+    int64_t max_gaussians;
+    int32_t max_views;
+    int64_t max_pixels;
+    int64_t max_pairs;
+    int64_t max_tiles;
+} splat_capacity;
+
+/* Loss weights (Eq. loss_full with rho_d = 1 and lambda_s = 0): o_eps floors O inside -log O. */
+typedef struct {
+    float lambda_n, lambda_o, o_eps;
+} splat_loss_config;
+
+/* Adam settings; one learning rate per parameter group. */
+typedef struct {
+    float lr_pos, lr_opacity, lr_rot, lr_scale;
+    float beta1, beta2, eps;
+} splat_adam_config;
+
+/* Counters of the last render / backward call (synchronising). */
+typedef struct {
+    int64_t n_pairs;          /* (tile, primitive) pairs binned, summed over views  */
+    int64_t fwd_evals;        /* pixel x primitive intersection tests in the forward */
+    int64_t bwd_evals;        /* the same in the backward                            */
+    int64_t n_pixels;         /* pixels of the registered views                      */
+    int64_t n_tiles;          /* tiles of the registered views                       */
+} splat_stats;
+
+/* ---- context ------------------------------------------------------------------------------ */
+
+/* Fill cfg with the defaults above (16x16 tiles). */
+SPLAT_API void splat_default_config(splat_render_config *cfg);
+
+/* Create a context on the current CUDA device and allocate its workspace (the only place the
+ * library allocates device memory).  *out receives the context.  Errors: INVALID_ARG (bad
+ * config or capacity), UNSUPPORTED (tile shape), CUDA (allocation failed). */
+SPLAT_API int splat_ctx_create(const splat_render_config *cfg, const splat_capacity *cap,
+                               splat_ctx **out);
+
+/* Free the context and its workspace (synchronises the device). NULL is ignored. */
+SPLAT_API void splat_ctx_destroy(splat_ctx *ctx);
+
+/* Register the views later calls render: n_views poses T_world_sensor (host, n_views x 16
+ * doubles, row-major sensor -> world) and intrinsics (host, n_views).  Uploads per-view tables
+ * synchronously; not for use under stream capture.  Errors: INVALID_ARG (n_views out of
+ * [1, max_views], non-finite or non-rigid pose, rows/cols outside [2, 32767], bad elevation
+ * range, more pixels or tiles than the capacity). */
+SPLAT_API int splat_set_views(splat_ctx *ctx, int32_t n_views, const double *T_world_sensor,
+                              const splat_lidar_intrinsics *intr);
+
+/* Pixel offset of view v in the packed image buffers (-1 if v is not registered). */
+SPLAT_API int64_t splat_view_pixel_offset(const splat_ctx *ctx, int32_t v);
+
+/* ---- render ------------------------------------------------------------------------------- */
+
+/* Render every registered view of the primitives g (g->n <= max_gaussians) into the packed
+ * buffers depth[P], normal[3][P], alpha[P] (device, caller-owned).  The per-tile lists,
+ * transmittances and contributor counts are kept in the context for the next backward call.
+ * Stages: per-primitive projection and spherical bounding box (one pass over all views),
+ * range sort, tile binning and sort, per-tile front-to-back compositing (one persistent launch
+ * over the tiles of all views).  Errors: INVALID_ARG, STATE (no views), CUDA. */
+SPLAT_API int splat_render_views(splat_ctx *ctx, const splat_gaussians *g, float *depth,
+                                 float *normal, float *alpha, void *stream);
+
+/* Gradient of L with respect to the parameters of the primitives rendered by the last
+ * splat_render_views / splat_render call of ctx, given dL/dD (P), dL/dN (3 x P) and dL/dO (P)
+ * in the packed layout (NULL means zero).  Writes g_pos_logit (n x 4: dL/dmu, dL/dlogit),
+ * g_quat (n x 4, w.r.t. the unnormalised quaternion) and g_log_scale (n x 2), summed over all
+ * views; accumulate = 1 adds to the existing contents instead of overwriting.  The back-to-front
+ * pass replays each pixel's composite, recovers the transmittance by division and reduces each
+ * primitive's per-pixel terms in a warp before one set of atomics per (tile, primitive).
+ * Errors: INVALID_ARG, STATE (no render before), CUDA. */
+SPLAT_API int splat_render_views_backward(splat_ctx *ctx, const splat_gaussians *g,
+                                          const float *dL_ddepth, const float *dL_dnormal,
+                                          const float *dL_dalpha, float *g_pos_logit,
+                                          float *g_quat, float *g_log_scale, int accumulate,
+                                          void *stream);
+
+/* One view: splat_set_views(ctx, 1, T_world_sensor, intr) followed by splat_render_views.  Not
+ * for stream capture (the view upload is synchronous). */
+SPLAT_API int splat_render(splat_ctx *ctx, const splat_gaussians *g,
+                           const double T_world_sensor[16], const splat_lidar_intrinsics *intr,
+                           float *depth, float *normal, float *alpha, void *stream);
+
+/* Same as splat_render_views_backward (the views are those of the last render). */
+SPLAT_API int splat_render_backward(splat_ctx *ctx, const splat_gaussians *g,
+                                    const float *dL_ddepth, const float *dL_dnormal,
+                                    const float *dL_dalpha, float *g_pos_logit, float *g_quat,
+                                    float *g_log_scale, int accumulate, void *stream);
+
+/* ---- loss and optimiser ------------------------------------------------------------------- */
+
+/* Per-pixel loss over n_pixels packed pixels (depth/alpha/target_depth [P], normal and
+ * target_normal [3][P] planar with plane stride n_pixels): valid pixels are those with
+ * target_depth > 0 (M_v); L = sum |D - Dt| + lambda_n (1 - N . Nt) + lambda_o (-log max(O,
+ * o_eps)).  Writes dL_ddepth, dL_dnormal (3 x P), dL_dalpha (0 outside M_v), and ADDS L to
+ * *loss_out (device double; caller zeroes it).  Errors: INVALID_ARG, CUDA. */
+SPLAT_API int splat_loss(const float *depth, const float *normal, const float *alpha,
+                         const float *target_depth, const float *target_normal,
+                         int64_t n_pixels, const splat_loss_config *cfg, float *dL_ddepth,
+                         float *dL_dnormal, float *dL_dalpha, double *loss_out, void *stream);
+
+/* One bias-corrected Adam step of n primitives in place: params (pos_logit, quat, log_scale),
+ * their gradients (same layout), first and second moments m_*, v_* (same layouts, caller-owned,
+ * zero before the first step) and a device int32 step counter that the call increments
+ * (the update uses t = *step + 1).  Errors: INVALID_ARG, CUDA. */
+SPLAT_API int splat_adam_step(float *pos_logit, float *quat, float *log_scale,
+                              const float *g_pos_logit, const float *g_quat,
+                              const float *g_log_scale, float *m_pos_logit, float *m_quat,
+                              float *m_log_scale, float *v_pos_logit, float *v_quat,
+                              float *v_log_scale, int32_t *step, int64_t n,
+                              const splat_adam_config *cfg, void *stream);
+
+/* One whole refinement iteration over the registered views, fused:
+ * render -> loss against the packed targets -> backward -> Adam, with the chain rule to the
+ * parameters fused into the Adam pass (no parameter-gradient buffers).  params are updated in
+ * place; m_* / v_* / step as in splat_adam_step; *loss_out receives (is overwritten with) the
+ * loss of this iteration.  Capturable in a CUDA graph (no host sync, no allocation).
+ * Errors: INVALID_ARG, STATE, CUDA. */
+SPLAT_API int splat_refine_step(splat_ctx *ctx, float *pos_logit, float *quat, float *log_scale,
+                                int64_t n, const float *target_depth, const float *target_normal,
+                                const splat_loss_config *loss_cfg,
+                                const splat_adam_config *adam_cfg, float *m_pos_logit,
+                                float *m_quat, float *m_log_scale, float *v_pos_logit,
+                                float *v_quat, float *v_log_scale, int32_t *step,
+                                double *loss_out, void *stream);
+
+/* ---- status, statistics, inspection ------------------------------------------------------- */
+
+/* Synchronise the device and read (then clear) the status word. */
+SPLAT_API int splat_get_status(splat_ctx *ctx, uint32_t *flags);
+
+/* Synchronise the device and read the counters of the last render / backward. */
+SPLAT_API int splat_get_stats(splat_ctx *ctx, splat_stats *out);
+
+/* Copy workspace state of the last render to host memory (synchronising), for tests and
+ * profiling.  which = 0: sorted global tile ids (uint32, n_pairs); 1: pair ids of the sorted
+ * list (uint32, n_pairs; pair id = view * n + primitive); 2: per-tile [start, end) (uint32 x 2 x
+ * n_tiles); 3: per-(view, primitive) records (16 bytes each: int16 row0, row1, col0, ncols;
+ * float32 kappa; uint32 bits 0-29 tile count, bit 30 normal flipped, bit 31 invalid input);
+ * 4: per-pixel final transmittance (float32, P); 5: per-pixel contributor bound (int32, P).
+ * bytes is the size of dst; returns the number of bytes copied, or -1 on error. */
+SPLAT_API int64_t splat_debug_copy(splat_ctx *ctx, int32_t which, void *dst, int64_t bytes);
+
+/* Text of a return code. */
+SPLAT_API const char *splat_error_string(int code);
+
+/* Text of the last CUDA error seen by any call (thread-local). */
+SPLAT_API const char *splat_last_cuda_error(void);
+
+/* Library version (major * 100 + minor). */
+SPLAT_API int splat_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SPLATLOAM_H */

@@ -83,6 +83,8 @@ def _load():
 
 
 def _ptr(a):
+    """Raw address of an array.  The caller keeps the array referenced until the C call returns:
+    a converted copy is bound to a local first, never passed inline as a temporary."""
     return None if a is None else a.ctypes.data
 
 
@@ -98,7 +100,8 @@ DEFAULT_CFG = (1.0 / 255.0, 0.99, 1e-4, 3.0)
 def pose_inverse(T_ws):
     R = np.zeros(9)
     t = np.zeros(3)
-    _load().or_pose_inverse(_ptr(_c(T_ws, np.float64)), _ptr(R), _ptr(t))
+    T = _c(T_ws, np.float64)
+    _load().or_pose_inverse(_ptr(T), _ptr(R), _ptr(t))
     return R.reshape(3, 3), t
 
 
@@ -124,7 +127,8 @@ def project_contract(pos_logit, quat, log_scale, T_ws, rows, cols, elev_min, ele
     til = np.zeros((n, 4), np.int32)
     cnt = np.zeros(n, np.int32)
     valid = np.zeros(n, np.uint8)
-    _load().or_project_contract(n, _ptr(pl), _ptr(q), _ptr(ls), _ptr(_c(T_ws, np.float64)),
+    T = _c(T_ws, np.float64)
+    _load().or_project_contract(n, _ptr(pl), _ptr(q), _ptr(ls), _ptr(T),
                                 rows, cols, float(np.float32(elev_min)),
                                 float(np.float32(elev_max)), tile_h, tile_w,
                                 float(np.float32(sigma_cut)), int(flip_normals),
@@ -204,9 +208,11 @@ def render(params, flip, order, T_ws, rows, cols, elev_min, elev_max, cfg=DEFAUL
     else:
         ts = te = ti = None
         th, tw = tile_h, tile_w
+    flip_a = _c(flip, np.int8)
+    Tw = _c(T_ws, np.float64)
     _load().or_render(n, _ptr(pos), _ptr(logit), _ptr(quat), _ptr(ls),
-                      _ptr(_c(flip, np.int8)), _ptr(order), len(order), _ptr(ts), _ptr(te),
-                      _ptr(ti), _ptr(_c(T_ws, np.float64)), rows, cols,
+                      _ptr(flip_a), _ptr(order), len(order), _ptr(ts), _ptr(te),
+                      _ptr(ti), _ptr(Tw), rows, cols,
                       float(elev_min), float(elev_max), th, tw, _ptr(cfg_a), _ptr(band_a),
                       _ptr(px), 0 if px is None else len(px),
                       _ptr(D), _ptr(N), _ptr(O), _ptr(T), _ptr(nc), _ptr(bf), n_threads)
@@ -233,12 +239,18 @@ def render_backward(params, flip, order, T_ws, rows, cols, elev_min, elev_max, g
     else:
         ts = te = ti = None
         th, tw = tile_h, tile_w
+    flip_a = _c(flip, np.int8)
+    Tw = _c(T_ws, np.float64)
+    cfg_a = _c(cfg, np.float64)
+    gD_a = _c(gD, np.float64).ravel()
+    gN_a = _c(gN, np.float64).ravel()
+    gO_a = _c(gO, np.float64).ravel()
     _load().or_render_backward(
-        n, _ptr(pos), _ptr(logit), _ptr(quat), _ptr(ls), _ptr(_c(flip, np.int8)), _ptr(order),
-        len(order), _ptr(ts), _ptr(te), _ptr(ti), _ptr(_c(T_ws, np.float64)), rows, cols,
-        float(elev_min), float(elev_max), th, tw, _ptr(np.asarray(cfg, np.float64)),
-        _ptr(px), 0 if px is None else len(px), _ptr(_c(gD, np.float64).ravel()), _ptr(_c(gN, np.float64).ravel()),
-        _ptr(_c(gO, np.float64).ravel()), _ptr(out["g_pos"]), _ptr(out["g_logit"]),
+        n, _ptr(pos), _ptr(logit), _ptr(quat), _ptr(ls), _ptr(flip_a), _ptr(order),
+        len(order), _ptr(ts), _ptr(te), _ptr(ti), _ptr(Tw), rows, cols,
+        float(elev_min), float(elev_max), th, tw, _ptr(cfg_a),
+        _ptr(px), 0 if px is None else len(px), _ptr(gD_a), _ptr(gN_a),
+        _ptr(gO_a), _ptr(out["g_pos"]), _ptr(out["g_logit"]),
         _ptr(out["g_quat"]), _ptr(out["g_log_scale"]), _ptr(out["g_b"]), _ptr(out["g_n"]),
         _ptr(out["g_o"]), n_threads)
     return out
@@ -252,9 +264,10 @@ def reach_pairs(params, T_ws, rows, cols, elev_min, elev_max, cfg=DEFAULT_CFG,
     n = pos.shape[0]
     pix = np.zeros(cap, np.int64)
     prim = np.zeros(cap, np.int32)
-    k = _load().or_reach_pairs(n, _ptr(pos), _ptr(logit), _ptr(quat), _ptr(ls),
-                               _ptr(_c(T_ws, np.float64)), rows, cols, float(elev_min),
-                               float(elev_max), _ptr(np.asarray(cfg, np.float64)), _ptr(pix),
+    Tw = _c(T_ws, np.float64)
+    cfg_a = _c(cfg, np.float64)
+    k = _load().or_reach_pairs(n, _ptr(pos), _ptr(logit), _ptr(quat), _ptr(ls), _ptr(Tw), rows,
+                               cols, float(elev_min), float(elev_max), _ptr(cfg_a), _ptr(pix),
                                _ptr(prim), cap)
     assert k <= cap
     return pix[:k], prim[:k]
@@ -263,14 +276,16 @@ def reach_pairs(params, T_ws, rows, cols, elev_min, elev_max, cfg=DEFAULT_CFG,
 def loss(D, N, O, Dt, Nt, lambda_n=1.0, lambda_o=0.0, o_eps=1e-6):
     """(L, gD, gN, gO) over flattened pixels; N, Nt are (3, npx) planar."""
     D = _c(D, np.float64).ravel()
+    N = _c(N, np.float64).ravel()
+    O = _c(O, np.float64).ravel()
+    Dt = _c(Dt, np.float64).ravel()
+    Nt = _c(Nt, np.float64).ravel()
     npx = D.size
     gD = np.zeros(npx)
     gN = np.zeros(3 * npx)
     gO = np.zeros(npx)
-    L = _load().or_loss(npx, _ptr(D), _ptr(_c(N, np.float64).ravel()),
-                        _ptr(_c(O, np.float64).ravel()), _ptr(_c(Dt, np.float64).ravel()),
-                        _ptr(_c(Nt, np.float64).ravel()), lambda_n, lambda_o, o_eps,
-                        _ptr(gD), _ptr(gN), _ptr(gO))
+    L = _load().or_loss(npx, _ptr(D), _ptr(N), _ptr(O), _ptr(Dt), _ptr(Nt), lambda_n, lambda_o,
+                        o_eps, _ptr(gD), _ptr(gN), _ptr(gO))
     return L, gD, gN.reshape(3, npx), gO
 
 
@@ -278,8 +293,8 @@ def adam(p, g, m, v, lr, b1=0.9, b2=0.999, eps=1e-15, step=1):
     """In-place FP64 Adam on 1-D float64 arrays."""
     for a in (p, m, v):
         assert a.dtype == np.float64 and a.flags.c_contiguous
-    _load().or_adam(p.size, _ptr(p), _ptr(_c(g, np.float64)), _ptr(m), _ptr(v), lr, b1, b2,
-                    eps, int(step))
+    g = _c(g, np.float64)
+    _load().or_adam(p.size, _ptr(p), _ptr(g), _ptr(m), _ptr(v), lr, b1, b2, eps, int(step))
 
 
 def full_view(pos_logit, quat, log_scale, T_ws, rows, cols, elev_min, elev_max, *,

@@ -1,0 +1,383 @@
+"""PyTorch-facing layer over the C ABI: tensors are used only as device memory and streams.
+
+* ``SplatContext`` -- owns a libsplatloam context (workspace sized at creation) and the views.
+* ``SplatRender`` -- ``torch.autograd.Function``: forward = splat_render_views, backward =
+  splat_render_views_backward.
+* ``loss`` / ``adam_step`` -- the loss and optimiser entry points.
+* ``Refiner`` -- one refinement iteration (render, loss, backward, Adam) over a set of keyframes,
+  either as plain per-keyframe launch sequences or as one fused pass over all keyframes captured
+  in a CUDA graph.
+
+Every tensor handed to the library must be a contiguous float32 CUDA tensor on the current
+device; the helpers check that and raise otherwise.
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+from dataclasses import dataclass
+
+import numpy as np
+import torch
+
+from . import _lib
+
+_P = ctypes.c_void_p
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if not (t.is_cuda and t.is_contiguous()):
+        raise ValueError("expected a contiguous CUDA tensor")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream=None):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _f32(t, shape_tail):
+    if t.dtype != torch.float32 or not t.is_cuda or not t.is_contiguous():
+        raise ValueError("expected contiguous float32 CUDA tensors")
+    if tuple(t.shape[1:]) != shape_tail:
+        raise ValueError(f"expected shape (n, {shape_tail})")
+    return t
+
+
+@dataclass
+class ViewSpec:
+    T_ws: np.ndarray
+    rows: int
+    cols: int
+    elev_min: float
+    elev_max: float
+
+
+@dataclass
+class RenderConfig:
+    alpha_min: float = 1.0 / 255.0
+    alpha_max: float = 0.99
+    t_min: float = 1e-4
+    sigma_cut: float = 3.0
+    tile_h: int = 16
+    tile_w: int = 16
+    flip_normals: int = 1
+
+    def c(self):
+        return _lib.splat_render_config(self.alpha_min, self.alpha_max, self.t_min,
+                                        self.sigma_cut, self.tile_h, self.tile_w, 0,
+                                        self.flip_normals)
+
+
+@dataclass
+class LossConfig:
+    lambda_n: float = 1.0
+    lambda_o: float = 0.0
+    o_eps: float = 1e-6
+
+    def c(self):
+        return _lib.splat_loss_config(self.lambda_n, self.lambda_o, self.o_eps)
+
+
+@dataclass
+class AdamConfig:
+    lr_pos: float = 1e-3
+    lr_opacity: float = 2e-2
+    lr_rot: float = 2e-3
+    lr_scale: float = 5e-3
+    beta1: float = 0.9
+    beta2: float = 0.999
+    eps: float = 1e-15
+
+    def c(self):
+        return _lib.splat_adam_config(self.lr_pos, self.lr_opacity, self.lr_rot, self.lr_scale,
+                                      self.beta1, self.beta2, self.eps)
+
+
+class SplatContext:
+    """A libsplatloam context: workspace for up to max_gaussians primitives, max_views views,
+    max_pixels packed pixels and max_pairs (tile, primitive) pairs per render call."""
+
+    def __init__(self, max_gaussians, max_views=1, max_pixels=1 << 20, max_pairs=None,
+                 cfg: RenderConfig | None = None, max_tiles=0):
+        self.lib = _lib.load()
+        self.cfg = cfg or RenderConfig()
+        if max_pairs is None:
+            max_pairs = min(max(16 * max_gaussians * max_views, 1 << 20), (1 << 32) - 1)
+        cap = _lib.splat_capacity(int(max_gaussians), int(max_views), int(max_pixels),
+                                  int(max_pairs), int(max_tiles))
+        h = ctypes.c_void_p()
+        torch.cuda.init()
+        _lib.check(self.lib.splat_ctx_create(ctypes.byref(self.cfg.c()), ctypes.byref(cap),
+                                             ctypes.byref(h)), "splat_ctx_create")
+        self.h = h
+        self.cap = cap
+        self.views: list[ViewSpec] = []
+        self.n_pixels = 0
+        self.offsets: list[int] = []
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.splat_ctx_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ---- views --------------------------------------------------------------------------
+    def set_views(self, views):
+        views = [v if isinstance(v, ViewSpec) else ViewSpec(np.asarray(v.T_ws), v.rows, v.cols,
+                                                             v.elev_min, v.elev_max)
+                 for v in views]
+        T = np.ascontiguousarray(np.stack([np.asarray(v.T_ws, np.float64) for v in views]))
+        intr = (_lib.splat_lidar_intrinsics * len(views))(
+            *[_lib.splat_lidar_intrinsics(v.rows, v.cols, v.elev_min, v.elev_max)
+              for v in views])
+        _lib.check(self.lib.splat_set_views(self.h, len(views), T.ctypes.data_as(_P), intr),
+                   "splat_set_views")
+        self.views = views
+        self.offsets = [int(self.lib.splat_view_pixel_offset(self.h, i))
+                        for i in range(len(views))]
+        self.n_pixels = sum(v.rows * v.cols for v in views)
+
+    def view_image(self, flat, v):
+        """(H, W) or (3, H, W) view of view v inside a packed (P,) or (3, P) tensor."""
+        vs = self.views[v]
+        o = self.offsets[v]
+        if flat.dim() == 1:
+            return flat[o:o + vs.rows * vs.cols].view(vs.rows, vs.cols)
+        return flat[:, o:o + vs.rows * vs.cols].reshape(3, vs.rows, vs.cols)
+
+    # ---- render / backward --------------------------------------------------------------
+    @staticmethod
+    def _g(pos_logit, quat, log_scale):
+        n = pos_logit.shape[0]
+        _f32(pos_logit, (4,))
+        _f32(quat, (4,))
+        _f32(log_scale, (2,))
+        if quat.shape[0] != n or log_scale.shape[0] != n:
+            raise ValueError("parameter tensors disagree on n")
+        return _lib.splat_gaussians(pos_logit.data_ptr(), quat.data_ptr(), log_scale.data_ptr(), n)
+
+    def alloc_images(self, device=None):
+        P = self.n_pixels
+        dev = device or torch.device("cuda")
+        return (torch.empty(P, device=dev), torch.empty(3, P, device=dev),
+                torch.empty(P, device=dev))
+
+    def render(self, pos_logit, quat, log_scale, out=None, stream=None):
+        depth, normal, alpha = out if out is not None else self.alloc_images(pos_logit.device)
+        g = self._g(pos_logit, quat, log_scale)
+        _lib.check(self.lib.splat_render_views(self.h, ctypes.byref(g), _ptr(depth), _ptr(normal),
+                                               _ptr(alpha), _stream(stream)),
+                   "splat_render_views")
+        return depth, normal, alpha
+
+    def backward(self, pos_logit, quat, log_scale, gD, gN, gO, out=None, accumulate=False,
+                 stream=None):
+        n = pos_logit.shape[0]
+        if out is None:
+            out = (torch.zeros(n, 4, device=pos_logit.device),
+                   torch.zeros(n, 4, device=pos_logit.device),
+                   torch.zeros(n, 2, device=pos_logit.device))
+        g = self._g(pos_logit, quat, log_scale)
+        _lib.check(self.lib.splat_render_views_backward(
+            self.h, ctypes.byref(g), _ptr(gD), _ptr(gN), _ptr(gO), _ptr(out[0]), _ptr(out[1]),
+            _ptr(out[2]), 1 if accumulate else 0, _stream(stream)), "splat_render_views_backward")
+        return out
+
+    def refine_step(self, params, state, target_depth, target_normal, loss_cfg: LossConfig,
+                    adam_cfg: AdamConfig, loss_out, stream=None):
+        pl, q, ls = params
+        m_pl, m_q, m_ls, v_pl, v_q, v_ls, step = state
+        _lib.check(self.lib.splat_refine_step(
+            self.h, _ptr(pl), _ptr(q), _ptr(ls), pl.shape[0], _ptr(target_depth),
+            _ptr(target_normal), ctypes.byref(loss_cfg.c()), ctypes.byref(adam_cfg.c()),
+            _ptr(m_pl), _ptr(m_q), _ptr(m_ls), _ptr(v_pl), _ptr(v_q), _ptr(v_ls), _ptr(step),
+            _ptr(loss_out), _stream(stream)), "splat_refine_step")
+
+    # ---- inspection ---------------------------------------------------------------------
+    def status(self) -> int:
+        f = ctypes.c_uint32(0)
+        _lib.check(self.lib.splat_get_status(self.h, ctypes.byref(f)), "splat_get_status")
+        return int(f.value)
+
+    def stats(self) -> dict:
+        s = _lib.splat_stats()
+        _lib.check(self.lib.splat_get_stats(self.h, ctypes.byref(s)), "splat_get_stats")
+        return dict(n_pairs=s.n_pairs, fwd_evals=s.fwd_evals, bwd_evals=s.bwd_evals,
+                    n_pixels=s.n_pixels, n_tiles=s.n_tiles)
+
+    def debug_copy(self, which: int, n_items: int, dtype) -> np.ndarray:
+        arr = np.zeros(n_items, dtype=dtype)
+        got = self.lib.splat_debug_copy(self.h, which, arr.ctypes.data_as(_P), arr.nbytes)
+        if got < 0:
+            raise _lib.SplatError("splat_debug_copy failed")
+        return arr[: got // arr.itemsize]
+
+    def sorted_lists(self):
+        """(sorted global tile ids, sorted pair ids, per-tile [start, end)) of the last render."""
+        st = self.stats()
+        m, nt = st["n_pairs"], st["n_tiles"]
+        keys = self.debug_copy(0, m, np.uint32)
+        vals = self.debug_copy(1, m, np.uint32)
+        ranges = self.debug_copy(2, 2 * nt, np.uint32).reshape(nt, 2)
+        return keys, vals, ranges
+
+    def pair_records(self, n):
+        """Per (view, primitive) records of the last render: r0, r1, c0, nc, kappa, count, flags."""
+        raw = self.debug_copy(3, 4 * n * len(self.views), np.uint32).reshape(-1, 4)
+        rc = raw[:, :2].copy().view(np.int16).reshape(-1, 4)
+        kappa = raw[:, 2].copy().view(np.float32)
+        cf = raw[:, 3]
+        return dict(r0=rc[:, 0], r1=rc[:, 1], c0=rc[:, 2], nc=rc[:, 3], kappa=kappa,
+                    count=(cf & 0x3FFFFFFF).astype(np.int64), flip=((cf >> 30) & 1).astype(bool),
+                    invalid=((cf >> 31) & 1).astype(bool))
+
+
+def loss(depth, normal, alpha, target_depth, target_normal, cfg: LossConfig | None = None,
+         stream=None):
+    """Per-pixel loss and its gradients over packed pixels; returns (L (device double tensor),
+    dL/dD, dL/dN, dL/dO)."""
+    cfg = cfg or LossConfig()
+    lib = _lib.load()
+    P = depth.shape[0]
+    gD = torch.empty_like(depth)
+    gN = torch.empty_like(normal)
+    gO = torch.empty_like(alpha)
+    L = torch.zeros(1, dtype=torch.float64, device=depth.device)
+    _lib.check(lib.splat_loss(_ptr(depth), _ptr(normal), _ptr(alpha), _ptr(target_depth),
+                              _ptr(target_normal), P, ctypes.byref(cfg.c()), _ptr(gD), _ptr(gN),
+                              _ptr(gO), _ptr(L), _stream(stream)), "splat_loss")
+    return L, gD, gN, gO
+
+
+def adam_state(n, device="cuda"):
+    z = lambda *s: torch.zeros(*s, device=device)  # noqa: E731
+    return (z(n, 4), z(n, 4), z(n, 2), z(n, 4), z(n, 4), z(n, 2),
+            torch.zeros(1, dtype=torch.int32, device=device))
+
+
+def adam_step(params, grads, state, cfg: AdamConfig | None = None, stream=None):
+    cfg = cfg or AdamConfig()
+    lib = _lib.load()
+    pl, q, ls = params
+    g_pl, g_q, g_ls = grads
+    m_pl, m_q, m_ls, v_pl, v_q, v_ls, step = state
+    _lib.check(lib.splat_adam_step(_ptr(pl), _ptr(q), _ptr(ls), _ptr(g_pl), _ptr(g_q), _ptr(g_ls),
+                                   _ptr(m_pl), _ptr(m_q), _ptr(m_ls), _ptr(v_pl), _ptr(v_q),
+                                   _ptr(v_ls), _ptr(step), pl.shape[0], ctypes.byref(cfg.c()),
+                                   _stream(stream)), "splat_adam_step")
+
+
+class SplatRender(torch.autograd.Function):
+    """(pos_logit, quat, log_scale) -> (depth (P,), normal (3,P), alpha (P,)) for the views
+    registered in the context; gradients through splat_render_views_backward."""
+
+    @staticmethod
+    def forward(ctx, pos_logit, quat, log_scale, sctx: SplatContext):
+        depth, normal, alpha = sctx.render(pos_logit, quat, log_scale)
+        ctx.sctx = sctx
+        ctx.save_for_backward(pos_logit, quat, log_scale)
+        return depth, normal, alpha
+
+    @staticmethod
+    def backward(ctx, gD, gN, gO):
+        pl, q, ls = ctx.saved_tensors
+        c = lambda t: None if t is None else t.contiguous()  # noqa: E731
+        g = ctx.sctx.backward(pl, q, ls, c(gD), c(gN), c(gO))
+        return g[0], g[1], g[2], None
+
+
+def render(pos_logit, quat, log_scale, sctx: SplatContext):
+    return SplatRender.apply(pos_logit, quat, log_scale, sctx)
+
+
+class Refiner:
+    """One map-refinement iteration over a set of keyframes sharing one map.
+
+    mode="batched": all keyframes in one fused pass (projection of every (keyframe, primitive),
+    one sort, persistent compositing over the tiles of all keyframes, loss, backward, fused
+    Adam), captured once in a CUDA graph and replayed.
+    mode="plain": one launch sequence per keyframe (render, loss, backward with accumulation),
+    then one Adam step -- no graph.
+    """
+
+    def __init__(self, params, views, targets, mode="batched", cfg: RenderConfig | None = None,
+                 loss_cfg: LossConfig | None = None, adam_cfg: AdamConfig | None = None,
+                 max_pairs=None):
+        self.params = params
+        self.n = params[0].shape[0]
+        self.views = list(views)
+        self.mode = mode
+        self.loss_cfg = loss_cfg or LossConfig()
+        self.adam_cfg = adam_cfg or AdamConfig()
+        dev = params[0].device
+        self.state = adam_state(self.n, dev)
+        P = sum(v.rows * v.cols for v in self.views)
+        if mode == "batched":
+            self.ctx = SplatContext(self.n, len(self.views), P, max_pairs, cfg)
+            self.ctx.set_views(self.views)
+            self.t_depth = torch.cat([t[0].reshape(-1) for t in targets]).contiguous()
+            self.t_normal = torch.cat([t[1].reshape(3, -1) for t in targets], 1).contiguous()
+            self.loss_out = torch.zeros(1, dtype=torch.float64, device=dev)
+        else:
+            maxp = max(v.rows * v.cols for v in self.views)
+            self.ctx = SplatContext(self.n, 1, maxp, max_pairs, cfg)
+            self.targets = [(t[0].reshape(-1).contiguous(), t[1].reshape(3, -1).contiguous())
+                            for t in targets]
+            self.grads = tuple(torch.zeros_like(p) for p in params)
+            self.loss_out = torch.zeros(1, dtype=torch.float64, device=dev)
+        self.graph = None
+
+    def _batched_step(self):
+        self.ctx.refine_step(self.params, self.state, self.t_depth, self.t_normal, self.loss_cfg,
+                             self.adam_cfg, self.loss_out)
+
+    def _plain_step(self):
+        self.loss_out.zero_()
+        for k, v in enumerate(self.views):
+            self.ctx.set_views([v])
+            d, nrm, a = self.ctx.render(*self.params)
+            L, gD, gN, gO = loss(d, nrm, a, self.targets[k][0], self.targets[k][1], self.loss_cfg)
+            self.loss_out += L
+            self.ctx.backward(*self.params, gD, gN, gO, out=self.grads, accumulate=k > 0)
+        adam_step(self.params, self.grads, self.state, self.adam_cfg)
+
+    def capture(self, warmup=2):
+        """Capture the batched iteration in a CUDA graph (after warm-up steps on a side stream)."""
+        assert self.mode == "batched"
+        s = torch.cuda.Stream()
+        s.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(s):
+            for _ in range(warmup):
+                self._batched_step()
+        torch.cuda.current_stream().wait_stream(s)
+        self.graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(self.graph):
+            self._batched_step()
+        return self.graph
+
+    def step(self):
+        if self.mode == "batched":
+            if self.graph is not None:
+                self.graph.replay()
+            else:
+                self._batched_step()
+        else:
+            self._plain_step()
+        return self.loss_out
+
+
+def default_capacity_pairs(n, views, per_prim=24):
+    """A generous (tile, primitive) pair capacity for n primitives over the given views."""
+    return int(min(max(per_prim * n * len(views), 1 << 20), (1 << 32) - 1))
+
+
+def n_tiles_of(views, th=16, tw=16):
+    return sum(math.ceil(v.rows / th) * math.ceil(v.cols / tw) for v in views)

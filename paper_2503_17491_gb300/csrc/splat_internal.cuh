@@ -1,0 +1,244 @@
+// Internal definitions shared by the translation units of libsplatloam (not part of the ABI).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "../../include/splatloam.h"
+
+namespace splat {
+
+constexpr int kMaxViews = 64;
+constexpr int kBlock = 256;          // threads per render CTA = pixels per tile
+
+// ---------------------------------------------------------------------------------------------
+// per-view descriptor (device)
+// ---------------------------------------------------------------------------------------------
+struct ViewDesc {
+    // T^c_w as float pairs (hi = nearest float of the FP64 value, lo = nearest float of the rest)
+    float R_hi[9], R_lo[9];       // row-major
+    float t_hi[3], t_lo[3];
+    int32_t rows, cols;
+    float elev_min, elev_max;
+    float kr;                     // binary32 (rows - 1) / (elev_max - elev_min): contract rows
+    float dgamma;                 // 2 pi / cols  (nearest float)
+    float dtheta;                 // (elev_max - elev_min) / (rows - 1)  (nearest float)
+    int32_t tiles_r, tiles_c;     // tile rows / columns of this view
+    int64_t tile_offset;          // first global tile id of the view
+    int64_t pixel_offset;         // first pixel of the view in the packed buffers
+    int32_t table_offset;         // into the frame table: tiles_r rows then tiles_c columns
+    int32_t pad_;
+};
+
+// Frame table entry (float pairs of FP64 sin / cos): per tile row sin/cos of the reference
+// elevation theta0, per tile column sin/cos of the reference azimuth gamma0.
+struct SinCos2 {
+    float s_hi, s_lo, c_hi, c_lo;
+};
+
+// Per (view, primitive) projection record, 16 bytes.
+struct PairRec {
+    int16_t r0, r1;   // pixel rows [r0, r1]
+    int16_t c0, nc;   // cyclic pixel columns [c0, c0 + nc) mod cols
+    float kappa;      // binary32 centre range |b_c|
+    uint32_t cf;      // bits 0-29: tiles touched; bit 30: normal flipped; bit 31: invalid input
+};
+static_assert(sizeof(PairRec) == 16, "PairRec is 16 bytes");
+
+enum : uint32_t { kCountMask = 0x3FFFFFFFu, kPairFlip = 1u << 30, kPairInvalid = 1u << 31 };
+
+// ---------------------------------------------------------------------------------------------
+// tile geometry shared by the binning and the render kernels
+// ---------------------------------------------------------------------------------------------
+
+// Cyclic tile-column range of a cyclic pixel-column range (integer arithmetic only).
+__host__ __device__ inline void tile_cols_of(int c0, int nc, int cols, int tw, int tiles_c,
+                                             int *tc0, int *ntc)
+{
+    if (nc >= cols) { *tc0 = 0; *ntc = tiles_c; return; }
+    int cl = c0 + nc - 1;
+    int a = c0 / tw;
+    int b = cl < cols ? cl / tw : tiles_c + (cl - cols) / tw;
+    int n = b - a + 1;
+    if (n >= tiles_c) { *tc0 = 0; *ntc = tiles_c; return; }
+    *tc0 = a;
+    *ntc = n;
+}
+
+// ---------------------------------------------------------------------------------------------
+// float-pair ("double-float") arithmetic, used where the sensor-frame centre of a primitive
+// must keep more than 24 bits (the lateral offset of a far splat from a ray).
+// ---------------------------------------------------------------------------------------------
+struct f2 {
+    float h, l;
+};
+
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e)
+{
+    s = __fadd_rn(a, b);
+    float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+__device__ __forceinline__ f2 f2_mul(f2 a, f2 b)
+{
+    float p = __fmul_rn(a.h, b.h);
+    float e = __fmaf_rn(a.h, b.h, -p);
+    e = __fmaf_rn(a.h, b.l, e);
+    e = __fmaf_rn(a.l, b.h, e);
+    f2 r;
+    two_sum(p, e, r.h, r.l);
+    return r;
+}
+
+__device__ __forceinline__ f2 f2_add(f2 a, f2 b)
+{
+    float s, e;
+    two_sum(a.h, b.h, s, e);
+    e = __fadd_rn(e, __fadd_rn(a.l, b.l));
+    f2 r;
+    two_sum(s, e, r.h, r.l);
+    return r;
+}
+
+__device__ __forceinline__ f2 f2_neg(f2 a) { return f2{-a.h, -a.l}; }
+
+// Sum_j M_j x_j + u in float-pair arithmetic, rounded to one float (x exact floats).
+__device__ __forceinline__ float f2_dot3_add(f2 m0, f2 m1, f2 m2, float x0, float x1, float x2,
+                                             f2 u)
+{
+    float p0 = __fmul_rn(m0.h, x0), e0 = __fmaf_rn(m0.h, x0, -p0);
+    float p1 = __fmul_rn(m1.h, x1), e1 = __fmaf_rn(m1.h, x1, -p1);
+    float p2 = __fmul_rn(m2.h, x2), e2 = __fmaf_rn(m2.h, x2, -p2);
+    float s1, t1, s2, t2, s3, t3;
+    two_sum(p0, p1, s1, t1);
+    two_sum(s1, p2, s2, t2);
+    two_sum(s2, u.h, s3, t3);
+    float err = __fadd_rn(__fadd_rn(e0, e1), e2);
+    err = __fadd_rn(err, __fadd_rn(__fadd_rn(t1, t2), t3));
+    err = __fmaf_rn(m0.l, x0, err);
+    err = __fmaf_rn(m1.l, x1, err);
+    err = __fmaf_rn(m2.l, x2, err);
+    err = __fadd_rn(err, u.l);
+    return __fadd_rn(s3, err);
+}
+
+// K7 for one primitive: world-frame accumulators (dL/dmu, dL/do | dL/dt_a, dL/dlog s_a |
+// dL/dt_b, dL/dlog s_b | dL/dt_n) -> gradients of (mu, logit), of the unnormalised quaternion
+// (through R(q/|q|)) and of the log-scales.
+__device__ __forceinline__ void chain_params(const float4 pl, const float4 q, const float4 *wg,
+                                             float4 &g_pl, float4 &g_q, float2 &g_ls)
+{
+    const float4 a0 = wg[0], a1 = wg[1], a2 = wg[2], a3 = wg[3];
+    const float qn2 = q.x * q.x + q.y * q.y + q.z * q.z + q.w * q.w;
+    const float rn = rsqrtf(qn2);
+    const float w = q.x * rn, x = q.y * rn, y = q.z * rn, z = q.w * rn;
+    // G[r][c] = dL/dR[r][c]; column c of R is t_a, t_b, t_n
+    const float G00 = a1.x, G10 = a1.y, G20 = a1.z;
+    const float G01 = a2.x, G11 = a2.y, G21 = a2.z;
+    const float G02 = a3.x, G12 = a3.y, G22 = a3.z;
+    const float gw = 2.0f * (z * (G10 - G01) + y * (G02 - G20) + x * (G21 - G12));
+    const float gx = 2.0f * (y * (G01 + G10) + z * (G02 + G20) + w * (G21 - G12)) -
+                     4.0f * x * (G11 + G22);
+    const float gy = 2.0f * (x * (G01 + G10) + w * (G02 - G20) + z * (G12 + G21)) -
+                     4.0f * y * (G00 + G22);
+    const float gz = 2.0f * (w * (G10 - G01) + x * (G02 + G20) + y * (G12 + G21)) -
+                     4.0f * z * (G00 + G11);
+    const float dotq = w * gw + x * gx + y * gy + z * gz;
+    g_q = make_float4((gw - w * dotq) * rn, (gx - x * dotq) * rn, (gy - y * dotq) * rn,
+                      (gz - z * dotq) * rn);
+    const float o = 1.0f / (1.0f + __expf(-pl.w));
+    g_pl = make_float4(a0.x, a0.y, a0.z, a0.w * o * (1.0f - o));
+    g_ls = make_float2(a1.w, a2.w);
+}
+
+// ---------------------------------------------------------------------------------------------
+// kernel launchers (defined in the .cu files)
+// ---------------------------------------------------------------------------------------------
+struct Workspace;   // host-side bookkeeping, defined in splat_abi.cu
+
+cudaError_t launch_project(const float4 *pos_logit, const float4 *quat, const float2 *log_scale,
+                           int64_t n, const ViewDesc *views, int n_views, float sigma, int tile_h,
+                           int tile_w, int flip_normals, PairRec *recs, uint32_t *dkeys,
+                           uint32_t *dvals, uint32_t *status, cudaStream_t st);
+
+// stable LSD radix sort of (uint32 key, uint32 value) pairs on key bits [0, bits);
+// the count is read on the device from *d_count (clamped to max_n); result lands in
+// (keys_out, vals_out).  tmp_hist holds kSortGrid * 256 uint32.
+constexpr int kSortGrid = 304;
+constexpr int kSortTile = 2048;   // keys per CTA tile (256 threads x 8)
+cudaError_t radix_sort_pairs(uint32_t *keys, uint32_t *vals, uint32_t *keys_alt, uint32_t *vals_alt,
+                             const uint32_t *d_count, int64_t max_n, int bits, uint32_t *tmp_hist,
+                             uint32_t **keys_out, uint32_t **vals_out, cudaStream_t st);
+
+// offsets of every sorted pair, emission of (global tile, pair id) entries, total pair count
+constexpr int kScanGrid = 304;
+cudaError_t launch_emit(const uint32_t *sorted_pair_ids, int64_t n_pairs_total, const PairRec *recs,
+                        const ViewDesc *views, int64_t n_per_view, int tile_h, int tile_w,
+                        uint32_t *block_sums, uint32_t *tile_keys, uint32_t *tile_vals,
+                        int64_t max_pairs, uint32_t *d_count, uint32_t *status, cudaStream_t st);
+
+cudaError_t launch_ranges(const uint32_t *tile_keys, const uint32_t *d_count, int64_t max_pairs,
+                          uint2 *ranges, int64_t n_tiles, cudaStream_t st);
+
+struct RenderArgs {
+    const float4 *pos_logit;
+    const float4 *quat;
+    const float2 *log_scale;
+    int64_t n;                    // primitives per view (pair id = view * n + i)
+    const ViewDesc *views;
+    const SinCos2 *frames;
+    const int32_t *tile_view;     // global tile -> view
+    const uint2 *ranges;          // global tile -> [start, end)
+    const uint32_t *sorted_vals;  // pair ids in (tile, range, id) order
+    const PairRec *recs;
+    int64_t n_tiles;
+    float alpha_min, alpha_max, t_min, sigma;
+    // forward outputs (packed pixels)
+    float *depth, *normal, *alpha;
+    int64_t n_pixels;
+    float *t_final;
+    int32_t *n_last;
+    // backward inputs / outputs
+    const float *g_depth, *g_normal, *g_alpha;
+    float4 *wgrad;                // per primitive 4 x float4 (world-frame accumulators)
+    uint32_t *queue;              // work counter (zeroed before each launch)
+    unsigned long long *evals;    // evaluation counter
+};
+
+cudaError_t launch_render_fwd(const RenderArgs &a, int tile_h, int tile_w, int grid,
+                              cudaStream_t st);
+cudaError_t launch_render_bwd(const RenderArgs &a, int tile_h, int tile_w, int grid,
+                              cudaStream_t st);
+int render_occupancy(int tile_h, int tile_w, bool backward);
+
+cudaError_t launch_param_grads(const float4 *pos_logit, const float4 *quat, const float2 *log_scale,
+                               const float4 *wgrad, int64_t n, float4 *g_pos_logit, float4 *g_quat,
+                               float2 *g_log_scale, int accumulate, cudaStream_t st);
+
+cudaError_t launch_loss(const float *depth, const float *normal, const float *alpha,
+                        const float *t_depth, const float *t_normal, int64_t n_pixels,
+                        float lambda_n, float lambda_o, float o_eps, float *g_depth,
+                        float *g_normal, float *g_alpha, double *loss_out, cudaStream_t st);
+
+struct AdamArgs {
+    float4 *pos_logit;
+    float4 *quat;
+    float2 *log_scale;
+    float4 *m_pl, *m_q;
+    float2 *m_ls;
+    float4 *v_pl, *v_q;
+    float2 *v_ls;
+    int32_t *step;
+    int64_t n;
+    float lr_pos, lr_opacity, lr_rot, lr_scale, beta1, beta2, eps;
+};
+
+// Adam from explicit parameter gradients
+cudaError_t launch_adam(const AdamArgs &a, const float4 *g_pl, const float4 *g_q,
+                        const float2 *g_ls, cudaStream_t st);
+// Adam with the chain rule from the world-frame accumulators fused in
+cudaError_t launch_adam_fused(const AdamArgs &a, const float4 *wgrad, cudaStream_t st);
+cudaError_t launch_step_inc(int32_t *step, cudaStream_t st);
+
+}  // namespace splat

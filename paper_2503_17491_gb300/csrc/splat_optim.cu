@@ -1,0 +1,177 @@
+// K8 (loss) and K9 (Adam, optionally fused with K7).
+//
+// Loss over the valid pixels M_v (target range > 0, Sec. 3.3.1): the L1 range term of
+// Eq. loss_range (rho_d = 1), the normal term of Eq. loss_normal taken against the target
+// normal, and optionally the opacity term of Eq. loss_opacity.  Per-pixel gradients are written
+// for the backward; the scalar is reduced per warp in binary32 and per CTA in binary64.
+//
+// Adam: the paper does not name its optimiser; a bias-corrected Adam with one learning rate per
+// parameter group is used.  The fused form applies the parameter chain rule (world-frame
+// accumulators -> d/dmu, d/dlogit, d/dq, d/dlog s) inside the update, so no parameter-gradient
+// buffer is written or read.  Both are HBM-bound streaming kernels (one primitive per thread,
+// 16-byte loads).
+
+#include "splat_internal.cuh"
+
+namespace splat {
+namespace {
+
+__global__ void __launch_bounds__(256) k_loss(const float *__restrict__ depth,
+                                              const float *__restrict__ normal,
+                                              const float *__restrict__ alpha,
+                                              const float *__restrict__ t_depth,
+                                              const float *__restrict__ t_normal, int64_t n,
+                                              float lambda_n, float lambda_o, float o_eps,
+                                              float *__restrict__ g_depth,
+                                              float *__restrict__ g_normal,
+                                              float *__restrict__ g_alpha,
+                                              double *__restrict__ loss_out)
+{
+    __shared__ double s_part[8];
+    float acc = 0.0f;
+    for (int64_t p = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; p < n;
+         p += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+        const float dt = t_depth[p];
+        float gd = 0.0f, gn0 = 0.0f, gn1 = 0.0f, gn2 = 0.0f, go = 0.0f;
+        if (dt > 0.0f) {
+            const float e = depth[p] - dt;
+            acc += fabsf(e);
+            gd = e > 0.0f ? 1.0f : (e < 0.0f ? -1.0f : 0.0f);
+            const float n0 = t_normal[p], n1 = t_normal[n + p], n2 = t_normal[2 * n + p];
+            const float dn = normal[p] * n0 + normal[n + p] * n1 + normal[2 * n + p] * n2;
+            acc += lambda_n * (1.0f - dn);
+            gn0 = -lambda_n * n0;
+            gn1 = -lambda_n * n1;
+            gn2 = -lambda_n * n2;
+            if (lambda_o != 0.0f) {
+                const float o = alpha[p];
+                acc += lambda_o * -logf(fmaxf(o, o_eps));
+                go = o > o_eps ? -lambda_o / o : 0.0f;
+            }
+        }
+        g_depth[p] = gd;
+        g_normal[p] = gn0;
+        g_normal[n + p] = gn1;
+        g_normal[2 * n + p] = gn2;
+        g_alpha[p] = go;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xFFFFFFFFu, acc, o);
+    if ((threadIdx.x & 31) == 0) s_part[threadIdx.x >> 5] = static_cast<double>(acc);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < 8; ++w) t += s_part[w];
+        atomicAdd(loss_out, t);
+    }
+}
+
+struct AdamScalars {
+    float c1, c2;   // bias corrections 1 - beta^t
+};
+
+__device__ __forceinline__ AdamScalars adam_scalars(const AdamArgs &a)
+{
+    const float t = static_cast<float>(*a.step + 1);
+    return AdamScalars{1.0f - powf(a.beta1, t), 1.0f - powf(a.beta2, t)};
+}
+
+__device__ __forceinline__ float adam1(float p, float g, float &m, float &v, float lr,
+                                       const AdamArgs &a, const AdamScalars &s)
+{
+    m = a.beta1 * m + (1.0f - a.beta1) * g;
+    v = a.beta2 * v + (1.0f - a.beta2) * g * g;
+    const float mh = m / s.c1, vh = v / s.c2;
+    return p - lr * mh / (sqrtf(vh) + a.eps);
+}
+
+__device__ __forceinline__ void adam_prim(const AdamArgs &a, int64_t i, float4 g_pl, float4 g_q,
+                                          float2 g_ls, const AdamScalars &s)
+{
+    float4 p = a.pos_logit[i], m = a.m_pl[i], v = a.v_pl[i];
+    p.x = adam1(p.x, g_pl.x, m.x, v.x, a.lr_pos, a, s);
+    p.y = adam1(p.y, g_pl.y, m.y, v.y, a.lr_pos, a, s);
+    p.z = adam1(p.z, g_pl.z, m.z, v.z, a.lr_pos, a, s);
+    p.w = adam1(p.w, g_pl.w, m.w, v.w, a.lr_opacity, a, s);
+    a.pos_logit[i] = p;
+    a.m_pl[i] = m;
+    a.v_pl[i] = v;
+    float4 q = a.quat[i], mq = a.m_q[i], vq = a.v_q[i];
+    q.x = adam1(q.x, g_q.x, mq.x, vq.x, a.lr_rot, a, s);
+    q.y = adam1(q.y, g_q.y, mq.y, vq.y, a.lr_rot, a, s);
+    q.z = adam1(q.z, g_q.z, mq.z, vq.z, a.lr_rot, a, s);
+    q.w = adam1(q.w, g_q.w, mq.w, vq.w, a.lr_rot, a, s);
+    a.quat[i] = q;
+    a.m_q[i] = mq;
+    a.v_q[i] = vq;
+    float2 l = a.log_scale[i], ml = a.m_ls[i], vl = a.v_ls[i];
+    l.x = adam1(l.x, g_ls.x, ml.x, vl.x, a.lr_scale, a, s);
+    l.y = adam1(l.y, g_ls.y, ml.y, vl.y, a.lr_scale, a, s);
+    a.log_scale[i] = l;
+    a.m_ls[i] = ml;
+    a.v_ls[i] = vl;
+}
+
+__global__ void __launch_bounds__(256) k_adam(const AdamArgs a, const float4 *__restrict__ g_pl,
+                                              const float4 *__restrict__ g_q,
+                                              const float2 *__restrict__ g_ls)
+{
+    const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (i >= a.n) return;
+    adam_prim(a, i, g_pl[i], g_q[i], g_ls[i], adam_scalars(a));
+}
+
+__global__ void __launch_bounds__(256) k_adam_fused(const AdamArgs a,
+                                                    const float4 *__restrict__ wgrad)
+{
+    const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (i >= a.n) return;
+    float4 gp, gq;
+    float2 gl;
+    chain_params(a.pos_logit[i], a.quat[i], wgrad + 4 * i, gp, gq, gl);
+    adam_prim(a, i, gp, gq, gl, adam_scalars(a));
+}
+
+__global__ void k_step_inc(int32_t *step)
+{
+    *step += 1;
+}
+
+}  // namespace
+
+cudaError_t launch_loss(const float *depth, const float *normal, const float *alpha,
+                        const float *t_depth, const float *t_normal, int64_t n_pixels,
+                        float lambda_n, float lambda_o, float o_eps, float *g_depth,
+                        float *g_normal, float *g_alpha, double *loss_out, cudaStream_t st)
+{
+    if (n_pixels <= 0) return cudaSuccess;
+    int64_t blocks = (n_pixels + 255) / 256;
+    if (blocks > 4096) blocks = 4096;
+    k_loss<<<static_cast<unsigned>(blocks), 256, 0, st>>>(depth, normal, alpha, t_depth, t_normal,
+                                                          n_pixels, lambda_n, lambda_o, o_eps,
+                                                          g_depth, g_normal, g_alpha, loss_out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_adam(const AdamArgs &a, const float4 *g_pl, const float4 *g_q,
+                        const float2 *g_ls, cudaStream_t st)
+{
+    if (a.n <= 0) return cudaSuccess;
+    k_adam<<<static_cast<unsigned>((a.n + 255) / 256), 256, 0, st>>>(a, g_pl, g_q, g_ls);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_adam_fused(const AdamArgs &a, const float4 *wgrad, cudaStream_t st)
+{
+    if (a.n <= 0) return cudaSuccess;
+    k_adam_fused<<<static_cast<unsigned>((a.n + 255) / 256), 256, 0, st>>>(a, wgrad);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_step_inc(int32_t *step, cudaStream_t st)
+{
+    k_step_inc<<<1, 1, 0, st>>>(step);
+    return cudaGetLastError();
+}
+
+}  // namespace splat

@@ -1,0 +1,287 @@
+// K1: per-primitive projection for every registered view -- the range key, the sign that turns
+// the normal towards the sensor, and the conservative spherical bounding box of the 3-sigma
+// parallelogram with its tile rectangle (Sec. 3.2.1 tiles and range sort; Sec. 3.2.3 bounding
+// box computation; Supp. B).
+//
+// Everything in this file takes integer decisions (which tiles, which order, which sign), so it
+// follows a fixed binary32 contract: every value is produced by the same sequence of correctly
+// rounded IEEE operations on every machine.  The file is compiled with -fmad=false so that no
+// a*b+c is fused; fused multiply-adds appear only where written as fmaf.  The arctangent and
+// exponential used by the contract are evaluated from their series (see contract_atan2 and
+// contract_exp), never through a math library.
+//
+// One thread per primitive reads its 40 bytes once (coalesced float4/float2 loads) and loops
+// over the views; each (view, primitive) record is 16 bytes.  The range-sort keys and pair ids
+// are written here too, so the sort starts from this kernel's output.
+
+#include <cmath>
+
+#include "splat_internal.cuh"
+
+namespace splat {
+namespace {
+
+constexpr float kPi = 3.14159274f;      // nearest binary32 values
+constexpr float kHalfPi = 1.57079637f;
+constexpr float kTwoPi = 6.28318548f;
+constexpr float kQuarterPi = 0.785398163f;
+constexpr float kTanPi8 = 0.414213562f;
+constexpr float kPixelMargin = 0.01f;   // pixel units, both axes
+
+// atan2 from the arctangent series: reduce to t = min/max in [0, 1], fold t > tan(pi/8) with
+// atan t = pi/4 + atan((t - 1)/(t + 1)), then z - z^3/3 + ... + z^17/17 on |z| <= tan(pi/8).
+__device__ float contract_atan2(float y, float x)
+{
+    const float ax = fabsf(x), ay = fabsf(y);
+    const float hi = ax > ay ? ax : ay;
+    const float lo = ax > ay ? ay : ax;
+    if (hi == 0.0f) return 0.0f;
+    const float t = lo / hi;
+    float z, base;
+    if (t > kTanPi8) {
+        z = (t - 1.0f) / (t + 1.0f);
+        base = kQuarterPi;
+    } else {
+        z = t;
+        base = 0.0f;
+    }
+    const float z2 = z * z;
+    float p = 0.0588235294f;
+    p = fmaf(p, z2, -0.0666666667f);
+    p = fmaf(p, z2, 0.0769230769f);
+    p = fmaf(p, z2, -0.0909090909f);
+    p = fmaf(p, z2, 0.111111111f);
+    p = fmaf(p, z2, -0.142857143f);
+    p = fmaf(p, z2, 0.2f);
+    p = fmaf(p, z2, -0.333333333f);
+    p = fmaf(p, z2, 1.0f);
+    float a = fmaf(z, p, base);
+    if (ay > ax) a = kHalfPi - a;
+    if (x < 0.0f) a = kPi - a;
+    if (y < 0.0f) a = -a;
+    return a;
+}
+
+// exp from a Cody-Waite split of ln 2 (2839/4096 plus its binary32 remainder) and the
+// exponential series through r^7/7!; 2^k is assembled in the exponent field.
+__device__ float contract_exp(float x)
+{
+    x = x > 80.0f ? 80.0f : x;
+    x = x < -80.0f ? -80.0f : x;
+    const float k = rintf(x * 1.44269504f);
+    const float r = (x - k * 0.693115234375f) - k * 3.19461849e-05f;
+    float p = 1.98412698e-04f;
+    p = fmaf(p, r, 1.38888889e-03f);
+    p = fmaf(p, r, 8.33333333e-03f);
+    p = fmaf(p, r, 4.16666667e-02f);
+    p = fmaf(p, r, 0.166666667f);
+    p = fmaf(p, r, 0.5f);
+    p = fmaf(p, r, 1.0f);
+    p = fmaf(p, r, 1.0f);
+    const int ki = static_cast<int>(k);
+    return p * __uint_as_float(static_cast<uint32_t>(ki + 127) << 23);
+}
+
+struct v3 {
+    float x, y, z;
+};
+
+// R v with R row-major, each row summed as ((a + b) + c)
+__device__ __forceinline__ v3 rot(const float *R, v3 v)
+{
+    return v3{(R[0] * v.x + R[1] * v.y) + R[2] * v.z, (R[3] * v.x + R[4] * v.y) + R[5] * v.z,
+              (R[6] * v.x + R[7] * v.y) + R[8] * v.z};
+}
+
+// Spherical bounding box of F = {b_c + a A + b B : |a|, |b| <= 1} with A = sigma b_alpha,
+// B = sigma b_beta.  Azimuth: every column when the z axis pierces the xy-shadow of F, else the
+// corner azimuths relative to the centre direction.  Elevation: corners, each edge's interior
+// extremum (where z / |xy| is stationary along the edge), and the pole the z axis reaches.
+// Returns the tile count and fills the record's pixel rectangle.
+__device__ uint32_t contract_bbox(v3 ba, v3 bb, v3 bc, float sigma, const ViewDesc &vd,
+                                  int tile_h, int tile_w, PairRec &rec)
+{
+    const v3 A{sigma * ba.x, sigma * ba.y, sigma * ba.z};
+    const v3 B{sigma * bb.x, sigma * bb.y, sigma * bb.z};
+    const v3 C = bc;
+    v3 P[4];
+    P[0] = v3{(C.x - A.x) - B.x, (C.y - A.y) - B.y, (C.z - A.z) - B.z};
+    P[1] = v3{(C.x + A.x) - B.x, (C.y + A.y) - B.y, (C.z + A.z) - B.z};
+    P[2] = v3{(C.x + A.x) + B.x, (C.y + A.y) + B.y, (C.z + A.z) + B.z};
+    P[3] = v3{(C.x - A.x) + B.x, (C.y - A.y) + B.y, (C.z - A.z) + B.z};
+
+    // does the z axis cross the xy-shadow of F?  c + a A + b B = 0 with |a|, |b| <= 1
+    const float det = A.x * B.y - A.y * B.x;
+    const float cxb = C.x * B.y - C.y * B.x;
+    const float axc = A.x * C.y - A.y * C.x;
+    const float la = fabsf(A.x) + fabsf(A.y), lb = fabsf(B.x) + fabsf(B.y);
+    const float lc = fabsf(C.x) + fabsf(C.y);
+    const float tol = 1e-5f * ((la + lb) * ((lc + la) + lb));
+    const float adet = fabsf(det);
+    const bool axis_in = (fabsf(cxb) <= adet + tol) && (fabsf(axc) <= adet + tol);
+    bool north = false, south = false;
+    if (axis_in) {
+        if (adet > tol) {
+            const float a = -cxb / det, b = -axc / det;
+            const float zh = (C.z + a * A.z) + b * B.z;
+            const float tz = 1e-5f * ((fabsf(C.z) + fabsf(A.z)) + fabsf(B.z));
+            north = zh > -tz;
+            south = zh < tz;
+        } else {
+            north = south = true;
+        }
+    }
+
+    float el_lo = INFINITY, el_hi = -INFINITY;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const v3 p = P[i], q = P[(i + 1) & 3];
+        const float e = contract_atan2(p.z, sqrtf(p.x * p.x + p.y * p.y));
+        el_lo = fminf(el_lo, e);
+        el_hi = fmaxf(el_hi, e);
+        const v3 d{q.x - p.x, q.y - p.y, q.z - p.z};
+        const float pd = p.x * d.x + p.y * d.y;
+        const float pp = p.x * p.x + p.y * p.y;
+        const float dd = d.x * d.x + d.y * d.y;
+        const float num = p.z * pd - d.z * pp;
+        const float den = d.z * pd - p.z * dd;
+        if (den != 0.0f) {
+            const float lam = num / den;
+            if (lam > 0.0f && lam < 1.0f) {
+                const v3 X{p.x + lam * d.x, p.y + lam * d.y, p.z + lam * d.z};
+                const float e2 = contract_atan2(X.z, sqrtf(X.x * X.x + X.y * X.y));
+                el_lo = fminf(el_lo, e2);
+                el_hi = fmaxf(el_hi, e2);
+            }
+        }
+    }
+    if (north) el_hi = kHalfPi;
+    if (south) el_lo = -kHalfPi;
+
+    const int H = vd.rows, W = vd.cols;
+    const float vhi = (vd.elev_max - el_hi) * vd.kr - kPixelMargin;
+    const float vlo = (vd.elev_max - el_lo) * vd.kr + kPixelMargin;
+    int r0 = static_cast<int>(ceilf(vhi));
+    int r1 = static_cast<int>(floorf(vlo));
+    r0 = r0 < 0 ? 0 : r0;
+    r1 = r1 > H - 1 ? H - 1 : r1;
+    if (r0 > r1) return 0u;
+
+    int c0, nc;
+    if (axis_in) {
+        c0 = 0;
+        nc = W;
+    } else {
+        const float gc = contract_atan2(C.y, C.x);
+        float dmin = INFINITY, dmax = -INFINITY;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const float cr = C.x * P[i].y - C.y * P[i].x;
+            const float dt = C.x * P[i].x + C.y * P[i].y;
+            const float dl = contract_atan2(cr, dt);
+            dmin = fminf(dmin, dl);
+            dmax = fmaxf(dmax, dl);
+        }
+        const float glo = gc + dmin, ghi = gc + dmax;
+        const float kc = static_cast<float>(W) / kTwoPi;
+        const float uf = ((kPi - ghi) * kc - 0.5f) - kPixelMargin;
+        const float ul = ((kPi - glo) * kc - 0.5f) + kPixelMargin;
+        const int cf = static_cast<int>(ceilf(uf));
+        const int cl = static_cast<int>(floorf(ul));
+        if (cf > cl) return 0u;
+        nc = cl - cf + 1;
+        if (nc >= W) {
+            c0 = 0;
+            nc = W;
+        } else {
+            c0 = ((cf % W) + W) % W;
+        }
+    }
+    int tc0, ntc;
+    tile_cols_of(c0, nc, W, tile_w, vd.tiles_c, &tc0, &ntc);
+    rec.r0 = static_cast<int16_t>(r0);
+    rec.r1 = static_cast<int16_t>(r1);
+    rec.c0 = static_cast<int16_t>(c0);
+    rec.nc = static_cast<int16_t>(nc);
+    return static_cast<uint32_t>((r1 / tile_h - r0 / tile_h + 1) * ntc);
+}
+
+__global__ void __launch_bounds__(256) k_project(
+    const float4 *__restrict__ pos_logit, const float4 *__restrict__ quat,
+    const float2 *__restrict__ log_scale, int64_t n, const ViewDesc *__restrict__ views,
+    int n_views, float sigma, int tile_h, int tile_w, int flip_normals, PairRec *__restrict__ recs,
+    uint32_t *__restrict__ dkeys, uint32_t *__restrict__ dvals, uint32_t *__restrict__ status)
+{
+    const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float4 pl = pos_logit[i];
+    const float4 q4 = quat[i];
+    const float2 ls = log_scale[i];
+
+    bool ok = isfinite(pl.x) && isfinite(pl.y) && isfinite(pl.z) && isfinite(pl.w) &&
+              isfinite(q4.x) && isfinite(q4.y) && isfinite(q4.z) && isfinite(q4.w) &&
+              isfinite(ls.x) && isfinite(ls.y);
+    // C1: normalised quaternion and scales
+    float w = q4.x, x = q4.y, y = q4.z, z = q4.w;
+    const float qq = ((w * w + x * x) + y * y) + z * z;
+    ok = ok && qq > 0.0f && isfinite(qq);
+    v3 ta{}, tb{}, tn{};
+    float sa = 0.0f, sb = 0.0f;
+    if (ok) {
+        const float r = sqrtf(qq);
+        w = w / r;
+        x = x / r;
+        y = y / r;
+        z = z / r;
+        // C2: rotation columns
+        ta = v3{1.0f - 2.0f * (y * y + z * z), 2.0f * (x * y + w * z), 2.0f * (x * z - w * y)};
+        tb = v3{2.0f * (x * y - w * z), 1.0f - 2.0f * (x * x + z * z), 2.0f * (y * z + w * x)};
+        tn = v3{2.0f * (x * z + w * y), 2.0f * (y * z - w * x), 1.0f - 2.0f * (x * x + y * y)};
+        sa = contract_exp(ls.x);
+        sb = contract_exp(ls.y);
+    } else {
+        atomicOr(status, SPLAT_STATUS_NONFINITE);
+    }
+    const v3 mu{pl.x, pl.y, pl.z};
+
+    for (int v = 0; v < n_views; ++v) {
+        const ViewDesc &vd = views[v];
+        const int64_t p = static_cast<int64_t>(v) * n + i;
+        PairRec rec;
+        rec.r0 = rec.r1 = rec.c0 = rec.nc = 0;
+        rec.kappa = 0.0f;
+        rec.cf = ok ? 0u : kPairInvalid;
+        if (ok) {
+            // C3: sensor frame with the binary32 T^c_w
+            const v3 ra = rot(vd.R_hi, ta), rb = rot(vd.R_hi, tb), rm = rot(vd.R_hi, mu);
+            const v3 ba{sa * ra.x, sa * ra.y, sa * ra.z};
+            const v3 bb{sb * rb.x, sb * rb.y, sb * rb.z};
+            const v3 bc{rm.x + vd.t_hi[0], rm.y + vd.t_hi[1], rm.z + vd.t_hi[2]};
+            const v3 nr = rot(vd.R_hi, tn);
+            const float dot = (nr.x * bc.x + nr.y * bc.y) + nr.z * bc.z;
+            if (flip_normals && dot > 0.0f) rec.cf |= kPairFlip;
+            rec.kappa = sqrtf((bc.x * bc.x + bc.y * bc.y) + bc.z * bc.z);
+            // C4: bounding box
+            rec.cf |= contract_bbox(ba, bb, bc, sigma, vd, tile_h, tile_w, rec);
+        }
+        recs[p] = rec;
+        dkeys[p] = (rec.cf & kCountMask) ? __float_as_uint(rec.kappa) : 0xFFFFFFFFu;
+        dvals[p] = static_cast<uint32_t>(p);
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_project(const float4 *pos_logit, const float4 *quat, const float2 *log_scale,
+                           int64_t n, const ViewDesc *views, int n_views, float sigma, int tile_h,
+                           int tile_w, int flip_normals, PairRec *recs, uint32_t *dkeys,
+                           uint32_t *dvals, uint32_t *status, cudaStream_t st)
+{
+    if (n <= 0) return cudaSuccess;
+    const unsigned grid = static_cast<unsigned>((n + 255) / 256);
+    k_project<<<grid, 256, 0, st>>>(pos_logit, quat, log_scale, n, views, n_views, sigma, tile_h,
+                                    tile_w, flip_normals, recs, dkeys, dvals, status);
+    return cudaGetLastError();
+}
+
+}  // namespace splat

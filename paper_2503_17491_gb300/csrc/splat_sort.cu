@@ -1,0 +1,337 @@
+// K2-K4: tile binning.
+//
+// The per-tile lists sorted by range (Sec. 3.2.1) are built in three steps:
+//   1. a stable radix sort of all (view, primitive) pairs by their binary32 range key
+//      (one key per pair, not per tile: far fewer keys than (tile, primitive) entries);
+//   2. emission, in that order, of one (global tile id, pair id) entry per touched tile, at
+//      offsets given by an exclusive scan of the tile counts (K2);
+//   3. a stable radix sort of the entries by tile id (K3).  Stability keeps step 1's order
+//      inside every tile, so each list ends up in (tile, range, id) order -- the same order as
+//      sorting 64-bit (tile << 32 | range bits) keys with the id as the final tie-break.
+// Tile ranges [start, end) follow from the sorted tile ids (K4).
+//
+// The sort is a reduce-then-scan LSD radix sort with 8-bit digits on a fixed grid of CTAs, so
+// that the element count can live on the device (it is data dependent after emission) and the
+// whole pipeline can be captured in a CUDA graph.  Ranking inside a CTA tile is warp-level
+// (match.any) and stable in (warp, item, lane) = index order.
+
+#include "splat_internal.cuh"
+
+namespace splat {
+namespace {
+
+constexpr int kRadix = 256;
+constexpr int kThreads = 256;
+constexpr int kItems = kSortTile / kThreads;   // 8
+constexpr int kWarps = kThreads / 32;
+
+__device__ __forceinline__ int64_t chunk_of(int64_t n, int grid)
+{
+    int64_t c = (n + grid - 1) / grid;
+    return (c + kSortTile - 1) / kSortTile * kSortTile;
+}
+
+__device__ __forceinline__ int64_t clamp_count(const uint32_t *d_count, int64_t max_n)
+{
+    int64_t n = d_count ? static_cast<int64_t>(*d_count) : max_n;
+    return n < max_n ? n : max_n;
+}
+
+// per-CTA digit histogram: hist[digit * grid + cta]
+__global__ void __launch_bounds__(kThreads) k_upsweep(const uint32_t *__restrict__ keys,
+                                                      const uint32_t *d_count, int64_t max_n,
+                                                      int shift, uint32_t *__restrict__ hist)
+{
+    __shared__ uint32_t s_cnt[kWarps][kRadix];
+    const int tid = threadIdx.x, warp = tid >> 5;
+    for (int k = tid; k < kWarps * kRadix; k += kThreads) (&s_cnt[0][0])[k] = 0;
+    __syncthreads();
+    const int64_t n = clamp_count(d_count, max_n);
+    const int64_t chunk = chunk_of(n, gridDim.x);
+    const int64_t begin = chunk * blockIdx.x;
+    const int64_t end = begin + chunk < n ? begin + chunk : n;
+    for (int64_t j = begin + tid; j < end; j += kThreads)
+        atomicAdd(&s_cnt[warp][(keys[j] >> shift) & 0xFF], 1u);
+    __syncthreads();
+    uint32_t t = 0;
+#pragma unroll
+    for (int w = 0; w < kWarps; ++w) t += s_cnt[w][tid];
+    hist[static_cast<int64_t>(tid) * gridDim.x + blockIdx.x] = t;
+}
+
+// exclusive scan of hist (kRadix * grid entries), one CTA of 1024 threads
+__global__ void __launch_bounds__(1024) k_scan_hist(uint32_t *__restrict__ hist, int total)
+{
+    __shared__ uint32_t s_part[1024];
+    const int tid = threadIdx.x;
+    const int per = (total + 1023) / 1024;
+    const int b = tid * per;
+    const int e = b + per < total ? b + per : total;
+    uint32_t sum = 0;
+    for (int k = b; k < e; ++k) sum += hist[k];
+    s_part[tid] = sum;
+    __syncthreads();
+    for (int off = 1; off < 1024; off <<= 1) {
+        uint32_t v = tid >= off ? s_part[tid - off] : 0u;
+        __syncthreads();
+        s_part[tid] += v;
+        __syncthreads();
+    }
+    uint32_t run = s_part[tid] - sum;
+    for (int k = b; k < e; ++k) {
+        uint32_t v = hist[k];
+        hist[k] = run;
+        run += v;
+    }
+}
+
+__global__ void __launch_bounds__(kThreads) k_downsweep(
+    const uint32_t *__restrict__ keys_in, const uint32_t *__restrict__ vals_in,
+    uint32_t *__restrict__ keys_out, uint32_t *__restrict__ vals_out, const uint32_t *d_count,
+    int64_t max_n, int shift, const uint32_t *__restrict__ hist)
+{
+    __shared__ uint32_t s_base[kRadix];          // running global offset per digit
+    __shared__ uint32_t s_wcnt[kWarps][kRadix];  // per-warp digit counts -> warp prefixes
+    __shared__ uint32_t s_tile[kRadix];          // digit totals of the current tile
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int64_t n = clamp_count(d_count, max_n);
+    const int64_t chunk = chunk_of(n, gridDim.x);
+    const int64_t begin = chunk * blockIdx.x;
+    const int64_t end = begin + chunk < n ? begin + chunk : n;
+    if (begin >= end) return;
+    s_base[tid] = hist[static_cast<int64_t>(tid) * gridDim.x + blockIdx.x];
+    const uint32_t lt_mask = (1u << lane) - 1u;
+
+    for (int64_t tb = begin; tb < end; tb += kSortTile) {
+        for (int k = tid; k < kWarps * kRadix; k += kThreads) (&s_wcnt[0][0])[k] = 0;
+        __syncthreads();
+        uint32_t key[kItems], val[kItems], rank[kItems];
+        int dig[kItems];
+#pragma unroll
+        for (int it = 0; it < kItems; ++it) {
+            const int64_t j = tb + warp * (32 * kItems) + it * 32 + lane;
+            const bool valid = j < end;
+            key[it] = valid ? keys_in[j] : 0u;
+            val[it] = valid ? vals_in[j] : 0u;
+            dig[it] = valid ? static_cast<int>((key[it] >> shift) & 0xFF) : kRadix + lane;
+            const uint32_t peers = __match_any_sync(0xFFFFFFFFu, dig[it]);
+            uint32_t before = 0;
+            if (valid) before = s_wcnt[warp][dig[it]];
+            __syncwarp();
+            rank[it] = before + __popc(peers & lt_mask);
+            const int last = 31 - __clz(peers);
+            if (valid && lane == last) s_wcnt[warp][dig[it]] = before + __popc(peers);
+            __syncwarp();
+        }
+        __syncthreads();
+        {   // digit tid: exclusive prefix over warps, tile total
+            uint32_t run = 0;
+#pragma unroll
+            for (int w = 0; w < kWarps; ++w) {
+                const uint32_t c = s_wcnt[w][tid];
+                s_wcnt[w][tid] = run;
+                run += c;
+            }
+            s_tile[tid] = run;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int it = 0; it < kItems; ++it) {
+            if (dig[it] < kRadix) {
+                const uint32_t pos = s_base[dig[it]] + s_wcnt[warp][dig[it]] + rank[it];
+                keys_out[pos] = key[it];
+                vals_out[pos] = val[it];
+            }
+        }
+        __syncthreads();
+        s_base[tid] += s_tile[tid];
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------------------------------------
+// emission (K2)
+// ---------------------------------------------------------------------------------------------
+
+__device__ __forceinline__ uint32_t pair_count(const PairRec *recs, uint32_t p)
+{
+    return recs[p].cf & kCountMask;
+}
+
+// per-CTA sums of the tile counts of its chunk of sorted pairs
+__global__ void __launch_bounds__(kThreads) k_count_sums(const uint32_t *__restrict__ sorted,
+                                                         int64_t n, const PairRec *__restrict__ recs,
+                                                         uint32_t *__restrict__ block_sums)
+{
+    __shared__ unsigned long long s_sum[kWarps];
+    const int64_t chunk = (n + gridDim.x - 1) / gridDim.x;
+    const int64_t b = chunk * blockIdx.x;
+    const int64_t e = b + chunk < n ? b + chunk : n;
+    unsigned long long sum = 0;
+    for (int64_t j = b + threadIdx.x; j < e; j += kThreads) sum += pair_count(recs, sorted[j]);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xFFFFFFFFu, sum, o);
+    if ((threadIdx.x & 31) == 0) s_sum[threadIdx.x >> 5] = sum;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned long long t = 0;
+        for (int w = 0; w < kWarps; ++w) t += s_sum[w];
+        block_sums[blockIdx.x] = t > 0xFFFFFFFFull ? 0xFFFFFFFFu : static_cast<uint32_t>(t);
+    }
+}
+
+// exclusive scan of the CTA sums (grid <= 1024 entries); total -> *d_count (saturated)
+__global__ void __launch_bounds__(1024) k_scan_sums(uint32_t *__restrict__ block_sums, int grid,
+                                                    int64_t max_pairs, uint32_t *d_count,
+                                                    uint32_t *status)
+{
+    __shared__ unsigned long long s[1024];
+    const int tid = threadIdx.x;
+    const unsigned long long v = tid < grid ? block_sums[tid] : 0ull;
+    s[tid] = v;
+    __syncthreads();
+    for (int off = 1; off < 1024; off <<= 1) {
+        const unsigned long long a = tid >= off ? s[tid - off] : 0ull;
+        __syncthreads();
+        s[tid] += a;
+        __syncthreads();
+    }
+    const unsigned long long excl = s[tid] - v;
+    if (tid < grid) block_sums[tid] = excl > 0xFFFFFFFFull ? 0xFFFFFFFFu : static_cast<uint32_t>(excl);
+    if (tid == 1023) {
+        const unsigned long long total = s[1023];
+        if (total > static_cast<unsigned long long>(max_pairs)) {
+            atomicOr(status, SPLAT_STATUS_CAPACITY);
+            *d_count = static_cast<uint32_t>(max_pairs);
+        } else {
+            *d_count = static_cast<uint32_t>(total);
+        }
+    }
+}
+
+// each thread emits the tiles of consecutive sorted pairs; offsets from a CTA scan
+__global__ void __launch_bounds__(kThreads) k_emit(
+    const uint32_t *__restrict__ sorted, int64_t n, const PairRec *__restrict__ recs,
+    const ViewDesc *__restrict__ views, int64_t n_per_view, int tile_h, int tile_w,
+    const uint32_t *__restrict__ block_base, uint32_t *__restrict__ tile_keys,
+    uint32_t *__restrict__ tile_vals, int64_t max_pairs)
+{
+    __shared__ uint32_t s_warp[kWarps];
+    __shared__ uint32_t s_carry;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int64_t chunk = (n + gridDim.x - 1) / gridDim.x;
+    const int64_t b = chunk * blockIdx.x;
+    const int64_t e = b + chunk < n ? b + chunk : n;
+    if (tid == 0) s_carry = block_base[blockIdx.x];
+    __syncthreads();
+    for (int64_t base = b; base < e; base += kThreads) {
+        const int64_t j = base + tid;
+        uint32_t p = 0, cnt = 0;
+        if (j < e) {
+            p = sorted[j];
+            cnt = pair_count(recs, p);
+        }
+        // block exclusive scan of cnt
+        uint32_t x = cnt;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, x, o);
+            if (lane >= o) x += y;
+        }
+        if (lane == 31) s_warp[warp] = x;
+        __syncthreads();
+        uint32_t wbase = 0, total = 0;
+#pragma unroll
+        for (int w = 0; w < kWarps; ++w) {
+            const uint32_t sw = s_warp[w];
+            wbase += w < warp ? sw : 0u;
+            total += sw;
+        }
+        const uint32_t off = s_carry + wbase + x - cnt;
+        if (cnt) {
+            const int v = static_cast<int>(p / n_per_view);
+            const ViewDesc &vd = views[v];
+            const PairRec rec = recs[p];
+            int tc0, ntc;
+            tile_cols_of(rec.c0, rec.nc, vd.cols, tile_w, vd.tiles_c, &tc0, &ntc);
+            const int tr0 = rec.r0 / tile_h, tr1 = rec.r1 / tile_h;
+            uint32_t k = 0;
+            for (int tr = tr0; tr <= tr1; ++tr) {
+                for (int c = 0; c < ntc; ++c, ++k) {
+                    const uint64_t o = static_cast<uint64_t>(off) + k;
+                    if (o >= static_cast<uint64_t>(max_pairs)) continue;
+                    int tc = tc0 + c;
+                    tc = tc >= vd.tiles_c ? tc - vd.tiles_c : tc;
+                    tile_keys[o] = static_cast<uint32_t>(vd.tile_offset + tr * vd.tiles_c + tc);
+                    tile_vals[o] = p;
+                }
+            }
+        }
+        __syncthreads();
+        if (tid == 0) s_carry += total;
+        __syncthreads();
+    }
+}
+
+// K4: [start, end) per tile from sorted tile ids (ranges zeroed before)
+__global__ void k_ranges(const uint32_t *__restrict__ keys, const uint32_t *d_count,
+                         int64_t max_pairs, uint2 *__restrict__ ranges)
+{
+    const int64_t m = clamp_count(d_count, max_pairs);
+    for (int64_t j = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; j < m;
+         j += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+        const uint32_t t = keys[j];
+        if (j == 0 || keys[j - 1] != t) ranges[t].x = static_cast<uint32_t>(j);
+        if (j == m - 1 || keys[j + 1] != t) ranges[t].y = static_cast<uint32_t>(j + 1);
+    }
+}
+
+}  // namespace
+
+cudaError_t radix_sort_pairs(uint32_t *keys, uint32_t *vals, uint32_t *keys_alt, uint32_t *vals_alt,
+                             const uint32_t *d_count, int64_t max_n, int bits, uint32_t *tmp_hist,
+                             uint32_t **keys_out, uint32_t **vals_out, cudaStream_t st)
+{
+    uint32_t *kin = keys, *vin = vals, *kout = keys_alt, *vout = vals_alt;
+    if (max_n > 0) {
+        for (int shift = 0; shift < bits; shift += 8) {
+            k_upsweep<<<kSortGrid, kThreads, 0, st>>>(kin, d_count, max_n, shift, tmp_hist);
+            k_scan_hist<<<1, 1024, 0, st>>>(tmp_hist, kSortGrid * kRadix);
+            k_downsweep<<<kSortGrid, kThreads, 0, st>>>(kin, vin, kout, vout, d_count, max_n, shift,
+                                                        tmp_hist);
+            uint32_t *t = kin;
+            kin = kout;
+            kout = t;
+            t = vin;
+            vin = vout;
+            vout = t;
+        }
+    }
+    *keys_out = kin;
+    *vals_out = vin;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_emit(const uint32_t *sorted_pair_ids, int64_t n_pairs_total, const PairRec *recs,
+                        const ViewDesc *views, int64_t n_per_view, int tile_h, int tile_w,
+                        uint32_t *block_sums, uint32_t *tile_keys, uint32_t *tile_vals,
+                        int64_t max_pairs, uint32_t *d_count, uint32_t *status, cudaStream_t st)
+{
+    k_count_sums<<<kScanGrid, kThreads, 0, st>>>(sorted_pair_ids, n_pairs_total, recs, block_sums);
+    k_scan_sums<<<1, 1024, 0, st>>>(block_sums, kScanGrid, max_pairs, d_count, status);
+    k_emit<<<kScanGrid, kThreads, 0, st>>>(sorted_pair_ids, n_pairs_total, recs, views, n_per_view,
+                                           tile_h, tile_w, block_sums, tile_keys, tile_vals,
+                                           max_pairs);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_ranges(const uint32_t *tile_keys, const uint32_t *d_count, int64_t max_pairs,
+                          uint2 *ranges, int64_t n_tiles, cudaStream_t st)
+{
+    cudaError_t e = cudaMemsetAsync(ranges, 0, sizeof(uint2) * static_cast<size_t>(n_tiles), st);
+    if (e != cudaSuccess) return e;
+    k_ranges<<<4 * kSortGrid, 256, 0, st>>>(tile_keys, d_count, max_pairs, ranges);
+    return cudaGetLastError();
+}
+
+}  // namespace splat

@@ -46,3 +46,22 @@ def test_adam_constant_gradient(oracle_mod):
         before = p.copy()
         oracle_mod.adam(p, g, m, v, lr=0.1, b1=0.9, b2=0.99, eps=1e-15, step=t)
         np.testing.assert_allclose(p - before, -0.1 * np.sign(g), rtol=1e-9)
+
+
+def test_loss_wrapper_with_converted_inputs(oracle_mod):
+    """float32 inputs are converted to float64 copies by the wrapper; those copies must stay alive
+    through the C call (a large case, so a freed copy would be overwritten)."""
+    rng = np.random.default_rng(0)
+    P = 5000
+    D = rng.uniform(0, 50, P).astype(np.float32)
+    N = rng.normal(size=(3, P)).astype(np.float32)
+    O = rng.uniform(0, 1, P).astype(np.float32)
+    Dt = np.where(rng.uniform(size=P) < 0.2, 0, rng.uniform(1, 50, P)).astype(np.float32)
+    Nt = rng.normal(size=(3, P)).astype(np.float32)
+    L, gD, gN, gO = oracle_mod.loss(D, N, O, Dt, Nt, lambda_n=0.5, lambda_o=0.1)
+    L2, *_ = oracle_mod.loss(D.astype(np.float64), N.astype(np.float64), O.astype(np.float64),
+                             Dt.astype(np.float64), Nt.astype(np.float64), lambda_n=0.5,
+                             lambda_o=0.1)
+    assert L == L2
+    v = Dt > 0
+    assert np.array_equal(gD != 0, v & (D != Dt))
