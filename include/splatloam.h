@@ -127,6 +127,7 @@ typedef struct {
     int64_t bwd_evals;        /* the same in the backward                            */
     int64_t n_pixels;         /* pixels of the registered views                      */
     int64_t n_tiles;          /* tiles of the registered views                       */
+    int64_t kernel_launches;  /* kernels this context has launched since creation    */
 } splat_stats;
 
 /* ---- context ------------------------------------------------------------------------------ */
@@ -235,6 +236,14 @@ SPLAT_API int splat_get_status(splat_ctx *ctx, uint32_t *flags);
 
 /* Synchronise the device and read the counters of the last render / backward. */
 SPLAT_API int splat_get_stats(splat_ctx *ctx, splat_stats *out);
+
+/* Profiling: when enabled, the next render / backward calls record CUDA events immediately
+ * before and after their compositing kernel (forward) and adjoint kernel (backward) on the call's
+ * stream; splat_kernel_times then returns those two kernels' durations in milliseconds (waiting
+ * for the events), or -1 for a kernel not recorded since profiling was enabled.  Calls made
+ * while the stream is being captured into a graph record nothing.  Errors: INVALID_ARG, CUDA. */
+SPLAT_API int splat_set_profiling(splat_ctx *ctx, int enable);
+SPLAT_API int splat_kernel_times(splat_ctx *ctx, float *fwd_ms, float *bwd_ms);
 
 /* Copy workspace state of the last render to host memory (synchronising), for tests and
  * profiling.  which = 0: sorted global tile ids (uint32, n_pairs); 1: pair ids of the sorted

@@ -51,7 +51,7 @@ class splat_adam_config(ctypes.Structure):
 
 class splat_stats(ctypes.Structure):
     _fields_ = [("n_pairs", _I64), ("fwd_evals", _I64), ("bwd_evals", _I64),
-                ("n_pixels", _I64), ("n_tiles", _I64)]
+                ("n_pixels", _I64), ("n_tiles", _I64), ("kernel_launches", _I64)]
 
 
 SPLAT_OK = 0
@@ -81,10 +81,13 @@ SIGNATURES = {
                     _P], _I),
     "splat_adam_step": ([_P] * 13 + [_I64, ctypes.POINTER(splat_adam_config), _P], _I),
     "splat_refine_step": ([_P, _P, _P, _P, _I64, _P, _P, ctypes.POINTER(splat_loss_config),
-                           ctypes.POINTER(splat_adam_config)] + [_P] * 9 + [_P], _I),
+                           ctypes.POINTER(splat_adam_config)] + [_P] * 9, _I),
     "splat_get_status": ([_P, ctypes.POINTER(ctypes.c_uint32)], _I),
     "splat_get_stats": ([_P, ctypes.POINTER(splat_stats)], _I),
     "splat_debug_copy": ([_P, _I32, _P, _I64], _I64),
+    "splat_set_profiling": ([_P, _I], _I),
+    "splat_kernel_times": ([_P, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_float)],
+                           _I),
 }
 
 _lib = None

@@ -211,7 +211,17 @@ class SplatContext:
         s = _lib.splat_stats()
         _lib.check(self.lib.splat_get_stats(self.h, ctypes.byref(s)), "splat_get_stats")
         return dict(n_pairs=s.n_pairs, fwd_evals=s.fwd_evals, bwd_evals=s.bwd_evals,
-                    n_pixels=s.n_pixels, n_tiles=s.n_tiles)
+                    n_pixels=s.n_pixels, n_tiles=s.n_tiles, kernel_launches=s.kernel_launches)
+
+    def set_profiling(self, on: bool):
+        _lib.check(self.lib.splat_set_profiling(self.h, 1 if on else 0), "splat_set_profiling")
+
+    def kernel_times(self):
+        """(forward compositing ms, backward adjoint ms) of the last profiled calls."""
+        f, b = ctypes.c_float(-1), ctypes.c_float(-1)
+        _lib.check(self.lib.splat_kernel_times(self.h, ctypes.byref(f), ctypes.byref(b)),
+                   "splat_kernel_times")
+        return float(f.value), float(b.value)
 
     def debug_copy(self, which: int, n_items: int, dtype) -> np.ndarray:
         arr = np.zeros(n_items, dtype=dtype)
@@ -381,3 +391,33 @@ def default_capacity_pairs(n, views, per_prim=24):
 
 def n_tiles_of(views, th=16, tw=16):
     return sum(math.ceil(v.rows / th) * math.ceil(v.cols / tw) for v in views)
+
+
+TILE_SHAPES = ((16, 16), (8, 32), (32, 8), (4, 64))
+
+
+def autotune_tile(params, views, targets, shapes=TILE_SHAPES, steps=3, max_pairs=None,
+                  loss_cfg: LossConfig | None = None, adam_cfg: AdamConfig | None = None):
+    """Pick the tile shape with the fastest batched refinement step on this workload.
+
+    Each candidate runs on a copy of the parameters: one warm-up step, then `steps` timed
+    steps (CUDA events).  Returns ((tile_h, tile_w), {shape: ms per step})."""
+    times = {}
+    for th, tw in shapes:
+        p = [t.clone() for t in params]
+        r = Refiner(p, views, targets, mode="batched", cfg=RenderConfig(tile_h=th, tile_w=tw),
+                    loss_cfg=loss_cfg, adam_cfg=adam_cfg, max_pairs=max_pairs)
+        r.step()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(steps):
+            r.step()
+        b.record()
+        torch.cuda.synchronize()
+        times[f"{th}x{tw}"] = a.elapsed_time(b) / steps
+        r.ctx.close()
+        del r, p
+    best = min(times, key=times.get)
+    th, tw = (int(x) for x in best.split("x"))
+    return (th, tw), times

@@ -90,6 +90,12 @@ struct splat_ctx {
     uint32_t *d_counters = nullptr;             // [0] pairs M, [1] status, [2] queue f, [3] queue b
     unsigned long long *d_evals = nullptr;      // [0] forward, [1] backward
 
+    // profiling events around the compositing kernels: [0,1] forward, [2,3] backward
+    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+    bool profiling = false;
+    bool rec_fwd = false, rec_bwd = false;
+    int64_t launches = 0;
+
     // state of the last render
     bool rendered = false;
     int64_t last_n = 0;
@@ -97,6 +103,12 @@ struct splat_ctx {
 };
 
 namespace {
+
+bool capturing(cudaStream_t st)
+{
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    return cudaStreamIsCapturing(st, &cs) == cudaSuccess && cs != cudaStreamCaptureStatusNone;
+}
 
 int check_gaussians(const splat_ctx *ctx, const splat_gaussians *g)
 {
@@ -168,7 +180,15 @@ int render_core(splat_ctx *ctx, const splat_gaussians *g, float *depth, float *n
     a.alpha = alpha;
     a.queue = cnt + 2;
     a.evals = ctx->d_evals;
+    const bool prof = ctx->profiling && !capturing(st);
+    if (prof) CK(cudaEventRecord(ctx->ev[0], st));
     CK(splat::launch_render_fwd(a, th, tw, ctx->grid_fwd, st));
+    if (prof) {
+        CK(cudaEventRecord(ctx->ev[1], st));
+        ctx->rec_fwd = true;
+    }
+    // project 1, range sort 4 x 3, emission 3, tile sort 3 per byte, ranges 1, composite 1
+    ctx->launches += 1 + 12 + 3 + 3 * (bits_for(ctx->n_tiles) / 8) + 1 + 1;
     ctx->rendered = true;
     ctx->last_n = n;
     return SPLAT_OK;
@@ -188,7 +208,14 @@ int backward_core(splat_ctx *ctx, const splat_gaussians *g, const float *gD, con
     a.g_alpha = gO;
     a.queue = cnt + 3;
     a.evals = ctx->d_evals + 1;
+    const bool prof = ctx->profiling && !capturing(st);
+    if (prof) CK(cudaEventRecord(ctx->ev[2], st));
     CK(splat::launch_render_bwd(a, ctx->cfg.tile_h, ctx->cfg.tile_w, ctx->grid_bwd, st));
+    if (prof) {
+        CK(cudaEventRecord(ctx->ev[3], st));
+        ctx->rec_bwd = true;
+    }
+    ctx->launches += 1;
     return SPLAT_OK;
 }
 
@@ -200,6 +227,8 @@ void free_ctx(splat_ctx *c)
                     c->d_img, c->d_gimg, c->d_counters, c->d_evals};
     for (void *p : ptrs)
         if (p) cudaFree(p);
+    for (cudaEvent_t e : c->ev)
+        if (e) cudaEventDestroy(e);
     delete c;
 }
 
@@ -290,6 +319,7 @@ SPLAT_API int splat_ctx_create(const splat_render_config *cfg, const splat_capac
     if (e == cudaSuccess) e = dalloc(&c->d_gimg, static_cast<size_t>(P) * 5);
     if (e == cudaSuccess) e = dalloc(&c->d_counters, 8);
     if (e == cudaSuccess) e = dalloc(&c->d_evals, 2);
+    for (int k = 0; k < 4 && e == cudaSuccess; ++k) e = cudaEventCreate(&c->ev[k]);
     if (e == cudaSuccess) e = cudaMemset(c->d_counters, 0, 8 * sizeof(uint32_t));
     if (e == cudaSuccess) e = cudaMemset(c->d_evals, 0, 2 * sizeof(unsigned long long));
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
@@ -445,6 +475,7 @@ SPLAT_API int splat_render_views_backward(splat_ctx *ctx, const splat_gaussians 
                                  reinterpret_cast<float4 *>(g_pos_logit),
                                  reinterpret_cast<float4 *>(g_quat),
                                  reinterpret_cast<float2 *>(g_log_scale), accumulate, st));
+    ctx->launches += 1;
     return SPLAT_OK;
 }
 
@@ -565,6 +596,7 @@ SPLAT_API int splat_refine_step(splat_ctx *ctx, float *pos_logit, float *quat, f
     a.eps = adam_cfg->eps;
     CK(splat::launch_adam_fused(a, ctx->d_wgrad, st));
     CK(splat::launch_step_inc(step, st));
+    ctx->launches += 3;   // loss, fused Adam, step counter
     return SPLAT_OK;
 }
 
@@ -590,6 +622,31 @@ SPLAT_API int splat_get_stats(splat_ctx *ctx, splat_stats *out)
     out->bwd_evals = static_cast<int64_t>(ev[1]);
     out->n_pixels = ctx->n_pixels;
     out->n_tiles = ctx->n_tiles;
+    out->kernel_launches = ctx->launches;
+    return SPLAT_OK;
+}
+
+SPLAT_API int splat_set_profiling(splat_ctx *ctx, int enable)
+{
+    if (!ctx) return SPLAT_ERR_INVALID_ARG;
+    ctx->profiling = enable != 0;
+    ctx->rec_fwd = ctx->rec_bwd = false;
+    return SPLAT_OK;
+}
+
+SPLAT_API int splat_kernel_times(splat_ctx *ctx, float *fwd_ms, float *bwd_ms)
+{
+    if (!ctx || !fwd_ms || !bwd_ms) return SPLAT_ERR_INVALID_ARG;
+    *fwd_ms = -1.0f;
+    *bwd_ms = -1.0f;
+    if (ctx->rec_fwd) {
+        CK(cudaEventSynchronize(ctx->ev[1]));
+        CK(cudaEventElapsedTime(fwd_ms, ctx->ev[0], ctx->ev[1]));
+    }
+    if (ctx->rec_bwd) {
+        CK(cudaEventSynchronize(ctx->ev[3]));
+        CK(cudaEventElapsedTime(bwd_ms, ctx->ev[2], ctx->ev[3]));
+    }
     return SPLAT_OK;
 }
 
