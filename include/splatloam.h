@@ -145,8 +145,9 @@ SPLAT_API int splat_ctx_create(const splat_render_config *cfg, const splat_capac
 SPLAT_API void splat_ctx_destroy(splat_ctx *ctx);
 
 /* Register the views later calls render: n_views poses T_world_sensor (host, n_views x 16
- * doubles, row-major sensor -> world) and intrinsics (host, n_views).  Uploads per-view tables
- * synchronously; not for use under stream capture.  Errors: INVALID_ARG (n_views out of
+ * doubles, row-major sensor -> world) and intrinsics (host, n_views).  Computes per-view tables
+ * (tile frames and per-pixel ray planes, in FP64) and uploads them synchronously, growing their
+ * device allocation when a larger view set needs it; not for use under stream capture.  Errors: INVALID_ARG (n_views out of
  * [1, max_views], non-finite or non-rigid pose, rows/cols outside [2, 32767], bad elevation
  * range, more pixels or tiles than the capacity). */
 SPLAT_API int splat_set_views(splat_ctx *ctx, int32_t n_views, const double *T_world_sensor,

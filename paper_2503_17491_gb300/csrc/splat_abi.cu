@@ -5,12 +5,15 @@
 
 #include <cmath>
 #include <cstdio>
+#include <algorithm>
 #include <cstring>
 #include <vector>
 
 #include "splat_internal.cuh"
 
 using splat::PairRec;
+using splat::PixFrame;
+using splat::TileInfo;
 using splat::SinCos2;
 using splat::ViewDesc;
 
@@ -75,6 +78,9 @@ struct splat_ctx {
     ViewDesc *d_views = nullptr;
     SinCos2 *d_frames = nullptr;
     int32_t *d_tile_view = nullptr;
+    PixFrame *d_pixframes = nullptr;   // grown by splat_set_views
+    int64_t pixframe_cap = 0;
+    TileInfo *d_tileinfo = nullptr;
 
     // workspace
     PairRec *d_recs = nullptr;
@@ -128,13 +134,13 @@ splat::RenderArgs render_args(splat_ctx *ctx, const splat_gaussians *g)
     a.quat = reinterpret_cast<const float4 *>(g->quat_wxyz);
     a.log_scale = reinterpret_cast<const float2 *>(g->log_scale);
     a.n = g->n;
-    a.views = ctx->d_views;
-    a.frames = ctx->d_frames;
-    a.tile_view = ctx->d_tile_view;
+    a.tiles = ctx->d_tileinfo;
+    a.pixframes = ctx->d_pixframes;
     a.ranges = ctx->d_ranges;
     a.sorted_vals = ctx->sorted_vals;
     a.recs = ctx->d_recs;
     a.n_tiles = ctx->n_tiles;
+    a.n_items = ctx->n_tiles * (splat::kBlock / 32);
     a.alpha_min = ctx->cfg.alpha_min;
     a.alpha_max = ctx->cfg.alpha_max;
     a.t_min = ctx->cfg.t_min;
@@ -224,7 +230,8 @@ void free_ctx(splat_ctx *c)
     void *ptrs[] = {c->d_views, c->d_frames, c->d_tile_view, c->d_recs, c->d_dkeys, c->d_dvals,
                     c->d_dkeys2, c->d_dvals2, c->d_tkeys, c->d_tvals, c->d_tkeys2, c->d_tvals2,
                     c->d_block_sums, c->d_hist, c->d_ranges, c->d_tfinal, c->d_nlast, c->d_wgrad,
-                    c->d_img, c->d_gimg, c->d_counters, c->d_evals};
+                    c->d_img, c->d_gimg, c->d_counters, c->d_evals, c->d_pixframes,
+                    c->d_tileinfo};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     for (cudaEvent_t e : c->ev)
@@ -300,6 +307,7 @@ SPLAT_API int splat_ctx_create(const splat_render_config *cfg, const splat_capac
     if (e == cudaSuccess) e = dalloc(&c->d_views, cap->max_views);
     if (e == cudaSuccess) e = dalloc(&c->d_frames, static_cast<size_t>(c->frame_cap) * 4);
     if (e == cudaSuccess) e = dalloc(&c->d_tile_view, TT);
+    if (e == cudaSuccess) e = dalloc(&c->d_tileinfo, TT);
     if (e == cudaSuccess) e = dalloc(&c->d_recs, mpv);
     if (e == cudaSuccess) e = dalloc(&c->d_dkeys, mpv);
     if (e == cudaSuccess) e = dalloc(&c->d_dvals, mpv);
@@ -349,6 +357,8 @@ SPLAT_API int splat_set_views(splat_ctx *ctx, int32_t n_views, const double *T_w
     const int th = ctx->cfg.tile_h, tw = ctx->cfg.tile_w;
     std::vector<ViewDesc> views(n_views);
     std::vector<SinCos2> frames;
+    std::vector<PixFrame> pixframes;
+    std::vector<TileInfo> tileinfo;
     std::vector<int32_t> tile_view;
     int64_t pix = 0, tiles = 0;
     for (int v = 0; v < n_views; ++v) {
@@ -416,6 +426,65 @@ SPLAT_API int splat_set_views(splat_ctx *ctx, int32_t n_views, const double *T_w
             split(std::cos(g0), e.c_hi, e.c_lo);
             frames.push_back(e);
         }
+        // pixel planes in the tile frame, in FP64 from exact small angle offsets:
+        // dg = gamma - gamma0, dt = theta - theta0, omc = 1 - cos(dg) = 2 sin^2(dg / 2)
+        vd.pix_offset = static_cast<int32_t>(pixframes.size());
+        for (int tr = 0; tr < vd.tiles_r; ++tr) {
+            const double t0 = emax - (tr * th + 0.5 * (th - 1)) * dth;
+            const double s0 = std::sin(t0), c0 = std::cos(t0);
+            for (int lr = 0; lr < th; ++lr)
+                for (int lc = 0; lc < tw; ++lc) {
+                    const double dt = -(lr - 0.5 * (th - 1)) * dth;
+                    const double dg = -(lc - 0.5 * (tw - 1)) * (2.0 * M_PI / in.cols);
+                    const double sg = std::sin(dg), cg = std::cos(dg);
+                    const double sh = std::sin(0.5 * dg), omc = 2.0 * sh * sh;
+                    const double sdt = std::sin(dt), cdt = std::cos(dt);
+                    const double sth = std::sin(t0 + dt), cth = std::cos(t0 + dt);
+                    const double hx[3] = {c0 * sg, cg, -s0 * sg};
+                    const double hy[3] = {-sdt + c0 * sth * omc, sth * sg, cdt - s0 * sth * omc};
+                    const double vv[3] = {cdt - c0 * cth * omc, -cth * sg, sdt + s0 * cth * omc};
+                    PixFrame f;
+                    std::memset(&f, 0, sizeof f);
+                    for (int k = 0; k < 3; ++k) {
+                        split(hx[k], f.hx[k], f.hx_lo[k]);
+                        split(hy[k], f.hy[k], f.hy_lo[k]);
+                        f.v[k] = static_cast<float>(vv[k]);
+                    }
+                    pixframes.push_back(f);
+                }
+        }
+        // per-tile frames: Q rows e1 = v(theta0, gamma0), e2 = h_x(gamma0), e3 = h_y(theta0,
+        // gamma0); M = Q R^c_w, u = Q t^c_w in FP64, stored as float pairs
+        for (int tr = 0; tr < vd.tiles_r; ++tr) {
+            const double t0 = emax - (tr * th + 0.5 * (th - 1)) * dth;
+            const double s0 = std::sin(t0), c0 = std::cos(t0);
+            for (int tc = 0; tc < vd.tiles_c; ++tc) {
+                const double g0 = M_PI - 2.0 * M_PI * (tc * tw + 0.5 * (tw - 1) + 0.5) / in.cols;
+                const double sg = std::sin(g0), cg = std::cos(g0);
+                const double Q[9] = {c0 * cg, c0 * sg, s0, sg, -cg, 0.0, -s0 * cg, -s0 * sg, c0};
+                TileInfo ti;
+                std::memset(&ti, 0, sizeof ti);
+                for (int r = 0; r < 3; ++r) {
+                    for (int c = 0; c < 3; ++c) {
+                        const double m = Q[3 * r] * Rcw[c] + Q[3 * r + 1] * Rcw[3 + c] +
+                                         Q[3 * r + 2] * Rcw[6 + c];
+                        split(m, ti.M_hi[3 * r + c], ti.M_lo[3 * r + c]);
+                    }
+                    const double u = Q[3 * r] * tcw[0] + Q[3 * r + 1] * tcw[1] + Q[3 * r + 2] * tcw[2];
+                    split(u, ti.u_hi[r], ti.u_lo[r]);
+                }
+                for (int k = 0; k < 9; ++k) ti.R[k] = vd.R_hi[k];
+                ti.view = v;
+                ti.tr = tr;
+                ti.tc = tc;
+                ti.cols = in.cols;
+                ti.valid_r = std::min(th, in.rows - tr * th);
+                ti.valid_c = std::min(tw, in.cols - tc * tw);
+                ti.pix_base = vd.pix_offset + tr * th * tw;
+                ti.out_base = pix + static_cast<int64_t>(tr) * th * in.cols + static_cast<int64_t>(tc) * tw;
+                tileinfo.push_back(ti);
+            }
+        }
         const int64_t nt = static_cast<int64_t>(vd.tiles_r) * vd.tiles_c;
         tile_view.insert(tile_view.end(), static_cast<size_t>(nt), v);
         tiles += nt;
@@ -429,6 +498,18 @@ SPLAT_API int splat_set_views(splat_ctx *ctx, int32_t n_views, const double *T_w
     CK(cudaMemcpy(ctx->d_frames, frames.data(), sizeof(SinCos2) * frames.size(),
                   cudaMemcpyHostToDevice));
     CK(cudaMemcpy(ctx->d_tile_view, tile_view.data(), sizeof(int32_t) * tile_view.size(),
+                  cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(ctx->d_tileinfo, tileinfo.data(), sizeof(TileInfo) * tileinfo.size(),
+                  cudaMemcpyHostToDevice));
+    if (static_cast<int64_t>(pixframes.size()) > ctx->pixframe_cap) {
+        CK(cudaDeviceSynchronize());
+        if (ctx->d_pixframes) CK(cudaFree(ctx->d_pixframes));
+        ctx->d_pixframes = nullptr;
+        ctx->pixframe_cap = 0;
+        CK(dalloc(&ctx->d_pixframes, pixframes.size()));
+        ctx->pixframe_cap = static_cast<int64_t>(pixframes.size());
+    }
+    CK(cudaMemcpy(ctx->d_pixframes, pixframes.data(), sizeof(PixFrame) * pixframes.size(),
                   cudaMemcpyHostToDevice));
     ctx->views = views;
     ctx->n_views = n_views;

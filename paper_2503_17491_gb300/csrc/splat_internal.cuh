@@ -27,7 +27,7 @@ struct ViewDesc {
     int64_t tile_offset;          // first global tile id of the view
     int64_t pixel_offset;         // first pixel of the view in the packed buffers
     int32_t table_offset;         // into the frame table: tiles_r rows then tiles_c columns
-    int32_t pad_;
+    int32_t pix_offset;           // into the pixel-frame table: tiles_r x 256 entries
 };
 
 // Frame table entry (float pairs of FP64 sin / cos): per tile row sin/cos of the reference
@@ -35,6 +35,32 @@ struct ViewDesc {
 struct SinCos2 {
     float s_hi, s_lo, c_hi, c_lo;
 };
+
+// Pixel ray planes of one pixel in its tile's frame (FP64 values as float pairs): h_x, h_y
+// (hi parts and the remainders) and the ray direction v (hi only).  One entry per (view, tile
+// row, pixel of the tile), 64 bytes.
+struct PixFrame {
+    float hx[3], hy[3], v[3];
+    float hx_lo[3], hy_lo[3];
+    float pad;
+};
+static_assert(sizeof(PixFrame) == 64, "PixFrame is 64 bytes");
+
+// Per-tile frame and addressing, computed on the host in FP64 when the views are registered.
+// The tile frame Q has rows e1 = v(theta0, gamma0) (the ray through the tile centre),
+// e2 = h_x(gamma0), e3 = h_y(theta0, gamma0); M = Q R^c_w and u = Q t^c_w as float pairs,
+// R^c_w rounded (normals are produced in the sensor frame).  192 bytes.
+struct TileInfo {
+    float M_hi[9], M_lo[9];
+    float u_hi[3], u_lo[3];
+    float R[9];
+    int32_t view, tr, tc, cols;      // cols: the view's width (row stride and cyclic period)
+    int32_t valid_r, valid_c;        // pixels of this tile inside the image
+    int32_t pix_base;                // first PixFrame entry of this tile row
+    int64_t out_base;                // packed index of the tile's top-left pixel
+    int32_t pad[6];
+};
+static_assert(sizeof(TileInfo) == 192, "TileInfo is 192 bytes");
 
 // Per (view, primitive) projection record, 16 bytes.
 struct PairRec {
@@ -123,6 +149,28 @@ __device__ __forceinline__ float f2_dot3_add(f2 m0, f2 m1, f2 m2, float x0, floa
     return __fadd_rn(s3, err);
 }
 
+// The same sum returned as a normalised float pair (hi = the rounded sum, lo = the rest).
+__device__ __forceinline__ f2 f2_dot3_add2(f2 m0, f2 m1, f2 m2, float x0, float x1, float x2,
+                                           f2 u)
+{
+    float p0 = __fmul_rn(m0.h, x0), e0 = __fmaf_rn(m0.h, x0, -p0);
+    float p1 = __fmul_rn(m1.h, x1), e1 = __fmaf_rn(m1.h, x1, -p1);
+    float p2 = __fmul_rn(m2.h, x2), e2 = __fmaf_rn(m2.h, x2, -p2);
+    float s1, t1, s2, t2, s3, t3;
+    two_sum(p0, p1, s1, t1);
+    two_sum(s1, p2, s2, t2);
+    two_sum(s2, u.h, s3, t3);
+    float err = __fadd_rn(__fadd_rn(e0, e1), e2);
+    err = __fadd_rn(err, __fadd_rn(__fadd_rn(t1, t2), t3));
+    err = __fmaf_rn(m0.l, x0, err);
+    err = __fmaf_rn(m1.l, x1, err);
+    err = __fmaf_rn(m2.l, x2, err);
+    err = __fadd_rn(err, u.l);
+    f2 r;
+    two_sum(s3, err, r.h, r.l);
+    return r;
+}
+
 // K7 for one primitive: world-frame accumulators (dL/dmu, dL/do | dL/dt_a, dL/dlog s_a |
 // dL/dt_b, dL/dlog s_b | dL/dt_n) -> gradients of (mu, logit), of the unnormalised quaternion
 // (through R(q/|q|)) and of the log-scales.
@@ -186,13 +234,13 @@ struct RenderArgs {
     const float4 *quat;
     const float2 *log_scale;
     int64_t n;                    // primitives per view (pair id = view * n + i)
-    const ViewDesc *views;
-    const SinCos2 *frames;
-    const int32_t *tile_view;     // global tile -> view
+    const TileInfo *tiles;        // global tile -> frame and addressing
+    const PixFrame *pixframes;
     const uint2 *ranges;          // global tile -> [start, end)
     const uint32_t *sorted_vals;  // pair ids in (tile, range, id) order
     const PairRec *recs;
     int64_t n_tiles;
+    int64_t n_items;              // n_tiles x blocks per tile
     float alpha_min, alpha_max, t_min, sigma;
     // forward outputs (packed pixels)
     float *depth, *normal, *alpha;

@@ -1,67 +1,67 @@
-// K5/K6 (+K10): per-tile front-to-back compositing and its back-to-front adjoint, as persistent
-// kernels over a work queue of (view, tile) items, and K7, the chain rule from the per-primitive
-// accumulators to the parameters.
+// K5/K6 (+K10): front-to-back compositing and its back-to-front adjoint as persistent kernels
+// over a work queue, and K7, the chain rule from the per-primitive accumulators to the
+// parameters.
 //
-// One CTA of 256 threads renders one tile of tile_h x tile_w = 256 pixels, one pixel per
-// thread.  The tile's primitives (its slice of the sorted list, Sec. 3.2.1) are staged into
-// shared memory 256 at a time -- each thread stages one primitive -- and every pixel then runs
-// through the batch.
+// Work decomposition.  A work item is one 4 x 8 pixel block of one tile (a tile is
+// tile_h x tile_w = 256 pixels, i.e. 8 blocks), taken by one warp, one pixel per lane; the queue
+// holds the blocks of every tile of every registered view, so many keyframes of uneven sizes
+// share one launch.  Warps never wait for one another: each walks its tile's slice of the
+// sorted list (Sec. 3.2.1) 32 entries at a time -- every lane reads one entry's projection
+// record, tests whether the primitive's pixel rectangle meets the warp's block, and the lanes
+// that hit stage their primitive into the warp's shared-memory slots -- then the warp evaluates
+// only the staged primitives, in list order (front to back in the forward, back to front in the
+// backward).  A warp leaves its block as soon as all its pixels are saturated.
 //
 // Numerics.  Each pixel ray is intersected with a splat as two planes h_x, h_y through the
 // sensor (Sec. 3.2.2, Eq. planes_to_splat; Supp. D.1): h_a = (h_x.b_a, h_x.b_b, h_x.b_c),
 // h_b likewise with h_y, p = h_a x h_b, s_hat = (p_x, p_y) / p_z.  The products h.b_c are lateral
-// offsets of the splat centre from the ray: a few centimetres out of up to 100 m of range, which
-// binary32 sensor-frame vectors cannot resolve (an f32 ulp at 64-128 m is 7.6e-6 m).  So every
-// tile gets its own orthonormal frame Q = (e1, e2, e3) -- e1 the ray through the tile centre, e2
-// and e3 its two planes -- and a primitive is staged as Q b in that frame, with Q R^c_w and
-// Q t^c_w kept as float pairs and the centre Q b_c formed in float-pair arithmetic before it is
-// rounded.  Inside the tile frame every pixel ray is within half a tile of e1, so h.b_c is a
-// difference of numbers of a few metres, not of a hundred.  The pixel planes in the tile frame
-// come from exact small angle offsets (integer pixel offsets times 2 pi / W and the row
-// spacing), so no large angle is ever rounded.
+// offsets of the splat centre from the pixel planes: centimetres out of up to 100 m of range,
+// which binary32 sensor-frame vectors cannot resolve.  So every tile has its own orthonormal
+// frame Q = (e1, e2, e3) -- e1 the ray through the tile centre, e2 and e3 its two planes -- and
+// a primitive is staged as Q b, with the centre Q b_c kept as a float pair; Q R^c_w, Q t^c_w and
+// the pixel planes in that frame come from tables computed in FP64 on the host (float pairs).
+// A pair first takes the binary32 box test with a 1% margin; only pairs that pass recompute
+// h_x.b_c and h_y.b_c in float-pair arithmetic (two-product / two-sum) and take the exact test,
+// so the costly path runs on hits only and grazing rays keep their accuracy.
 //
 // The range is d = nu . v (nu lies on the ray, so this equals |nu| without a square root) and
-// a hit counts only when d > 0 (in front of the sensor).  The cutoffs follow the 3DGS
-// conventions (alpha clamp, alpha_min, stop before T < t_min) plus the 3-sigma box test
-// max |s_hat| <= sigma, written as max(|p_x|, |p_y|) <= sigma |p_z| so that misses need no
-// division.  A per-(tile, primitive) pixel rectangle from the bounding box skips most misses
-// with two integer compares.
+// a hit counts only when d > 0 (in front of the sensor).  Cutoffs: alpha clamped at alpha_max,
+// skipped below alpha_min, stop before T < t_min, and max |s_hat| <= sigma written as
+// max(|p_x|, |p_y|) <= sigma |p_z| so that misses need no division.
 //
-// Forward and backward evaluate a (pixel, primitive) pair with the same explicitly rounded
-// operations (no contraction choices left to the compiler), so the backward replays exactly
-// the contributor set of the forward.  The backward recovers T_k = T_{k+1} / (1 - alpha_k) from
-// the final transmittance, keeps the suffix sums B_{d,k}, B_{n,k}, B_{o,k} of Supp. D.2, sums
-// each primitive's 13 per-pixel terms across the warp with shuffles, then across the CTA in
-// shared memory, rotates them back to the world frame once per (tile, primitive) and issues
-// four float4 atomics into a per-primitive accumulator (view independent, so gradients of many
-// views add up directly).
+// Forward and backward evaluate a pair with the same explicitly rounded operations, so the
+// backward replays exactly the contributor set of the forward.  The backward recovers
+// T_k = T_{k+1} / (1 - alpha_k) from the final transmittance, keeps the suffix sums B_{d,k},
+// B_{n,k}, B_{o,k} of Supp. D.2, sums each primitive's 13 per-pixel terms over the warp (a
+// shuffle tree, or direct shared-memory atomics when only a few lanes contribute) into the
+// primitive's slot, and the lane that staged the primitive rotates the slot back to the world
+// frame and issues four float4 atomics into a per-primitive accumulator (view independent, so
+// gradients of many views add up directly).
 
 #include "splat_internal.cuh"
 
 namespace splat {
 namespace {
 
-struct __align__(16) Staged {
-    float4 a;   // b_alpha' (tile frame), o
-    float4 b;   // b_beta' (tile frame), packed pixel rectangle (bits)
-    float4 c;   // c' = Q b_c (tile frame), alpha clamp flag unused
-    float4 n;   // normal (sensor frame)
-};
+constexpr float kLooseBox = 1.01f;   // margin of the binary32 pre-test
+constexpr int kDirectLanes = 6;      // up to this many contributing lanes: direct smem atomics
+constexpr int kWarps = kBlock / 32;  // warps per CTA (independent)
+constexpr int kBlocksPerTile = kBlock / 32;
 
-struct TileFrame {
-    f2 M[9];        // Q R^c_w, row-major
-    f2 u[3];        // Q t^c_w
-    float Mh[9];    // hi parts
-    float Rh[9];    // R^c_w hi parts (normals stay in the sensor frame)
-    int view;
-    int tr, tc;
-    int pad_;
+struct __align__(16) Staged {
+    float4 a;    // b_alpha' (tile frame), o
+    float4 b;    // b_beta' (tile frame), packed pixel rectangle (bits)
+    float4 c;    // c' = Q b_c, hi part (tile frame)
+    float4 lo;   // c' remainder
+    float4 n;    // normal (sensor frame)
 };
 
 struct Pix {
     float hx0, hx1, hx2;
     float hy0, hy1, hy2;
     float v0, v1, v2;
+    float hxl0, hxl1, hxl2;
+    float hyl0, hyl1, hyl2;
 };
 
 __device__ __forceinline__ float dot3e(float a0, float a1, float a2, float b0, float b1, float b2)
@@ -69,98 +69,60 @@ __device__ __forceinline__ float dot3e(float a0, float a1, float a2, float b0, f
     return __fmaf_rn(a0, b0, __fmaf_rn(a1, b1, __fmul_rn(a2, b2)));
 }
 
-// tile frame: rows e1 = v(theta0, gamma0), e2 = h_x(gamma0), e3 = h_y(theta0, gamma0)
-__device__ void build_frame(const ViewDesc &vd, const SinCos2 *frames, int tr, int tc, int tid,
-                            TileFrame &tf)
+// h . c with h and c as float pairs, rounded once at the end: the products are formed exactly
+// (two-product), the two largest -- which cancel -- are summed exactly (two-sum).
+__device__ __forceinline__ float dot3_f2(float h0, float h1, float h2, float l0, float l1,
+                                         float l2, const float4 &c, const float4 &cl)
 {
-    const SinCos2 rowf = frames[vd.table_offset + tr];
-    const SinCos2 colf = frames[vd.table_offset + vd.tiles_r + tc];
-    const f2 st{rowf.s_hi, rowf.s_lo}, ct{rowf.c_hi, rowf.c_lo};
-    const f2 sg{colf.s_hi, colf.s_lo}, cg{colf.c_hi, colf.c_lo};
-    if (tid < 12) {
-        const int k = tid < 9 ? tid / 3 : tid - 9;   // row of Q
-        f2 q[3];
-        if (k == 0) {
-            q[0] = f2_mul(ct, cg);
-            q[1] = f2_mul(ct, sg);
-            q[2] = st;
-        } else if (k == 1) {
-            q[0] = sg;
-            q[1] = f2_neg(cg);
-            q[2] = f2{0.0f, 0.0f};
-        } else {
-            q[0] = f2_neg(f2_mul(st, cg));
-            q[1] = f2_neg(f2_mul(st, sg));
-            q[2] = ct;
-        }
-        if (tid < 9) {
-            const int j = tid % 3;
-            f2 acc{0.0f, 0.0f};
-#pragma unroll
-            for (int m = 0; m < 3; ++m)
-                acc = f2_add(acc, f2_mul(q[m], f2{vd.R_hi[3 * m + j], vd.R_lo[3 * m + j]}));
-            tf.M[tid] = acc;
-            tf.Mh[tid] = acc.h + acc.l;
-        } else {
-            f2 acc{0.0f, 0.0f};
-#pragma unroll
-            for (int m = 0; m < 3; ++m)
-                acc = f2_add(acc, f2_mul(q[m], f2{vd.t_hi[m], vd.t_lo[m]}));
-            tf.u[k] = acc;
-        }
-    } else if (tid < 21) {
-        tf.Rh[tid - 12] = vd.R_hi[tid - 12];
-    }
+    const float p0 = __fmul_rn(h0, c.x), e0 = __fmaf_rn(h0, c.x, -p0);
+    const float p1 = __fmul_rn(h1, c.y), e1 = __fmaf_rn(h1, c.y, -p1);
+    const float p2 = __fmul_rn(h2, c.z), e2 = __fmaf_rn(h2, c.z, -p2);
+    float s, t, s2, t2;
+    two_sum(p0, p1, s, t);
+    two_sum(s, p2, s2, t2);
+    float err = __fadd_rn(__fadd_rn(e0, e1), __fadd_rn(e2, __fadd_rn(t, t2)));
+    err = __fmaf_rn(h0, cl.x, err);
+    err = __fmaf_rn(h1, cl.y, err);
+    err = __fmaf_rn(h2, cl.z, err);
+    err = __fmaf_rn(l0, c.x, err);
+    err = __fmaf_rn(l1, c.y, err);
+    err = __fmaf_rn(l2, c.z, err);
+    return __fadd_rn(s2, err);
 }
 
-template <int TH, int TW>
-__device__ __forceinline__ Pix pixel_frame(const ViewDesc &vd, const SinCos2 *frames, int tr,
-                                           int lr, int lc)
+__device__ __forceinline__ Pix load_pix(const PixFrame *table, int index)
 {
-    const SinCos2 rowf = frames[vd.table_offset + tr];
-    const float s0 = rowf.s_hi, c0 = rowf.c_hi;
-    const float dlc = static_cast<float>(lc) - 0.5f * static_cast<float>(TW - 1);
-    const float dlr = static_cast<float>(lr) - 0.5f * static_cast<float>(TH - 1);
-    const float dg = -vd.dgamma * dlc;   // gamma - gamma0
-    const float dt = -vd.dtheta * dlr;   // theta - theta0
-    float sg, cg, sdt, cdt;
-    sincosf(dg, &sg, &cg);
-    sincosf(dt, &sdt, &cdt);
-    const float sh = sinf(0.5f * dg);
-    const float omc = 2.0f * sh * sh;      // 1 - cos(dg) without cancellation
-    const float sth = s0 * cdt + c0 * sdt; // sin(theta)
-    const float cth = c0 * cdt - s0 * sdt; // cos(theta)
+    const float4 *e = reinterpret_cast<const float4 *>(table + index);
+    const float4 a = e[0], b = e[1], c = e[2], d = e[3];
     Pix p;
-    p.hx0 = c0 * sg;
-    p.hx1 = cg;
-    p.hx2 = -s0 * sg;
-    p.hy0 = -sdt + c0 * sth * omc;
-    p.hy1 = sth * sg;
-    p.hy2 = cdt - s0 * sth * omc;
-    p.v0 = cdt - c0 * cth * omc;
-    p.v1 = -cth * sg;
-    p.v2 = sdt + s0 * cth * omc;
+    p.hx0 = a.x; p.hx1 = a.y; p.hx2 = a.z;
+    p.hy0 = a.w; p.hy1 = b.x; p.hy2 = b.y;
+    p.v0 = b.z; p.v1 = b.w; p.v2 = c.x;
+    p.hxl0 = c.y; p.hxl1 = c.z; p.hxl2 = c.w;
+    p.hyl0 = d.x; p.hyl1 = d.y; p.hyl2 = d.z;
     return p;
 }
 
-// pixel rectangle of a primitive inside the tile, packed as 4 bytes (r_lo, r_hi, c_lo, c_hi)
+// pixel rectangle of a primitive inside the tile, packed as 4 bytes (r_lo, r_hi, c_lo, c_hi);
+// the record's columns are cyclic modulo the image width
 template <int TH, int TW>
-__device__ __forceinline__ uint32_t local_rect(const PairRec &rec, const ViewDesc &vd, int tr,
-                                               int tc)
+__device__ __forceinline__ uint32_t local_rect(const PairRec &rec, const TileInfo &ti)
 {
-    const int rb = tr * TH, cb = tc * TW;
+    const int rb = ti.tr * TH, cb = ti.tc * TW;
     int r_lo = rec.r0 - rb, r_hi = rec.r1 - rb;
     r_lo = r_lo < 0 ? 0 : r_lo;
     r_hi = r_hi > TH - 1 ? TH - 1 : r_hi;
     if (r_lo > r_hi) return 0xFFu;   // empty: r_lo = 255 > r_hi = 0
-    const int W = vd.cols, nc = rec.nc;
+    const int W = ti.cols, nc = rec.nc;
     int c_lo, c_hi;
     if (nc >= W) {
         c_lo = 0;
         c_hi = TW - 1;
     } else {
-        const int d = ((cb - rec.c0) % W + W) % W;      // tile start relative to the range start
-        const int e = ((rec.c0 - cb) % W + W) % W;      // range start relative to the tile start
+        int d = cb - rec.c0;     // tile start relative to the range start, in [0, W)
+        d += d < 0 ? W : 0;
+        int e = rec.c0 - cb;     // range start relative to the tile start, in [0, W)
+        e += e < 0 ? W : 0;
         const bool start_in = d < nc;
         const bool begins_here = e < TW;
         if (start_in && begins_here && d != 0) {   // both ends of a wrapping range meet here
@@ -189,17 +151,25 @@ __device__ __forceinline__ bool in_rect(uint32_t rect, int lr, int lc)
     return lr >= r_lo && lr <= r_hi && lc >= c_lo && lc <= c_hi;
 }
 
+// does the rectangle overlap the 4 x 8 block with top-left (br, bc)?
+__device__ __forceinline__ bool rect_meets_block(uint32_t rect, int br, int bc)
+{
+    const int r_lo = rect & 0xFF, r_hi = (rect >> 8) & 0xFF;
+    const int c_lo = (rect >> 16) & 0xFF, c_hi = rect >> 24;
+    return r_lo <= br + 3 && r_hi >= br && c_lo <= bc + 7 && c_hi >= bc;
+}
+
 struct Prim {
     int64_t i;
     float sa, sb;
     bool flip;
 };
 
-// stage pair id p of the current tile into the tile frame
-__device__ __forceinline__ void stage(const RenderArgs &A, const TileFrame &tf, uint32_t p,
+// stage pair id p of the tile into the tile frame
+__device__ __forceinline__ void stage(const RenderArgs &A, const TileInfo &ti, uint32_t p,
                                       const PairRec &rec, uint32_t rect, Staged &out, Prim &pr)
 {
-    const int64_t i = static_cast<int64_t>(p) - static_cast<int64_t>(tf.view) * A.n;
+    const int64_t i = static_cast<int64_t>(p) - static_cast<int64_t>(ti.view) * A.n;
     const float4 pl = A.pos_logit[i];
     const float4 q = A.quat[i];
     const float2 ls = A.log_scale[i];
@@ -213,17 +183,23 @@ __device__ __forceinline__ void stage(const RenderArgs &A, const TileFrame &tf, 
                 tn2 = 1.0f - 2.0f * (x * x + y * y);
     const float sa = __expf(ls.x), sb = __expf(ls.y);
     const float o = 1.0f / (1.0f + __expf(-pl.w));
-    const float *M = tf.Mh;
+    const float *M = ti.M_hi;
     out.a = make_float4(sa * (M[0] * ta0 + M[1] * ta1 + M[2] * ta2),
                         sa * (M[3] * ta0 + M[4] * ta1 + M[5] * ta2),
                         sa * (M[6] * ta0 + M[7] * ta1 + M[8] * ta2), o);
     out.b = make_float4(sb * (M[0] * tb0 + M[1] * tb1 + M[2] * tb2),
                         sb * (M[3] * tb0 + M[4] * tb1 + M[5] * tb2),
                         sb * (M[6] * tb0 + M[7] * tb1 + M[8] * tb2), __uint_as_float(rect));
-    out.c = make_float4(f2_dot3_add(tf.M[0], tf.M[1], tf.M[2], pl.x, pl.y, pl.z, tf.u[0]),
-                        f2_dot3_add(tf.M[3], tf.M[4], tf.M[5], pl.x, pl.y, pl.z, tf.u[1]),
-                        f2_dot3_add(tf.M[6], tf.M[7], tf.M[8], pl.x, pl.y, pl.z, tf.u[2]), 0.0f);
-    const float *R = tf.Rh;
+    f2 c[3];
+#pragma unroll
+    for (int r = 0; r < 3; ++r)
+        c[r] = f2_dot3_add2(f2{ti.M_hi[3 * r], ti.M_lo[3 * r]},
+                            f2{ti.M_hi[3 * r + 1], ti.M_lo[3 * r + 1]},
+                            f2{ti.M_hi[3 * r + 2], ti.M_lo[3 * r + 2]}, pl.x, pl.y, pl.z,
+                            f2{ti.u_hi[r], ti.u_lo[r]});
+    out.c = make_float4(c[0].h, c[1].h, c[2].h, 0.0f);
+    out.lo = make_float4(c[0].l, c[1].l, c[2].l, 0.0f);
+    const float *R = ti.R;
     const float fs = (rec.cf & kPairFlip) ? -1.0f : 1.0f;
     out.n = make_float4(fs * (R[0] * tn0 + R[1] * tn1 + R[2] * tn2),
                         fs * (R[3] * tn0 + R[4] * tn1 + R[5] * tn2),
@@ -251,10 +227,18 @@ __device__ __forceinline__ bool evaluate(const Staged &s, const Pix &px, float s
     h.hb1 = dot3e(px.hy0, px.hy1, px.hy2, s.b.x, s.b.y, s.b.z);
     h.hb2 = dot3e(px.hy0, px.hy1, px.hy2, s.c.x, s.c.y, s.c.z);
     h.pz = __fmaf_rn(h.ha0, h.hb1, -__fmul_rn(h.ha1, h.hb0));
+    const float pxx = __fmaf_rn(h.ha1, h.hb2, -__fmul_rn(h.ha2, h.hb1));
+    const float pyy = __fmaf_rn(h.ha2, h.hb0, -__fmul_rn(h.ha0, h.hb2));
+    const float apz = fabsf(h.pz);
+    if (!(apz > 0.0f) ||
+        !(fmaxf(fabsf(pxx), fabsf(pyy)) <= __fmul_rn(sigma * kLooseBox, apz)))
+        return false;
+    // precise lateral offsets of the centre from the two pixel planes
+    h.ha2 = dot3_f2(px.hx0, px.hx1, px.hx2, px.hxl0, px.hxl1, px.hxl2, s.c, s.lo);
+    h.hb2 = dot3_f2(px.hy0, px.hy1, px.hy2, px.hyl0, px.hyl1, px.hyl2, s.c, s.lo);
     h.px = __fmaf_rn(h.ha1, h.hb2, -__fmul_rn(h.ha2, h.hb1));
     h.py = __fmaf_rn(h.ha2, h.hb0, -__fmul_rn(h.ha0, h.hb2));
-    const float apz = fabsf(h.pz);
-    if (!(apz > 0.0f) || !(fmaxf(fabsf(h.px), fabsf(h.py)) <= __fmul_rn(sigma, apz))) return false;
+    if (!(fmaxf(fabsf(h.px), fabsf(h.py)) <= __fmul_rn(sigma, apz))) return false;
     h.inv = __frcp_rn(h.pz);
     h.sa = __fmul_rn(h.px, h.inv);
     h.sb = __fmul_rn(h.py, h.inv);
@@ -280,8 +264,48 @@ __device__ __forceinline__ unsigned long long block_sum_u64(unsigned long long v
     __syncthreads();
     unsigned long long t = 0;
     if (threadIdx.x == 0)
-        for (int w = 0; w < kBlock / 32; ++w) t += s_red[w];
+        for (int w = 0; w < kWarps; ++w) t += s_red[w];
     return t;
+}
+
+// the next work item of this warp (lane 0 takes it from the queue)
+__device__ __forceinline__ uint32_t next_item(uint32_t *queue, int lane)
+{
+    uint32_t it = 0;
+    if (lane == 0) it = atomicAdd(queue, 1u);
+    return __shfl_sync(0xFFFFFFFFu, it, 0);
+}
+
+// copy the tile's 192-byte record into the warp's shared slot
+__device__ __forceinline__ void load_tile(const TileInfo *tiles, int64_t tile, TileInfo &dst,
+                                         int lane)
+{
+    const float4 *src = reinterpret_cast<const float4 *>(tiles + tile);
+    float4 *d = reinterpret_cast<float4 *>(&dst);
+    if (lane < 12) d[lane] = src[lane];
+    __syncwarp();
+}
+
+struct BlockPix {
+    int br, bc, lr, lc;
+    bool inside;
+    int64_t out;     // packed pixel index
+    int pf;          // pixel-frame entry
+};
+
+template <int TH, int TW>
+__device__ __forceinline__ BlockPix block_pixel(const TileInfo &ti, int blk, int lane)
+{
+    constexpr int WC = TW / 8;
+    BlockPix b;
+    b.br = (blk / WC) * 4;
+    b.bc = (blk % WC) * 8;
+    b.lr = b.br + (lane >> 3);
+    b.lc = b.bc + (lane & 7);
+    b.inside = b.lr < ti.valid_r && b.lc < ti.valid_c;
+    b.out = ti.out_base + static_cast<int64_t>(b.lr) * ti.cols + b.lc;
+    b.pf = ti.pix_base + b.lr * TW + b.lc;
+    return b;
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -290,88 +314,82 @@ __device__ __forceinline__ unsigned long long block_sum_u64(unsigned long long v
 template <int TH, int TW>
 __global__ void __launch_bounds__(kBlock, 3) k_render_fwd(const RenderArgs A)
 {
-    static_assert(TH * TW == kBlock, "one pixel per thread");
-    __shared__ Staged s_st[kBlock];
-    __shared__ TileFrame s_tf;
-    __shared__ int64_t s_tile;
-    __shared__ unsigned long long s_red[kBlock / 32];
-    const int tid = threadIdx.x;
-    const int lr = tid / TW, lc = tid % TW;
+    static_assert(TH * TW == kBlock && TH % 4 == 0 && TW % 8 == 0, "4x8 warp blocks");
+    __shared__ Staged s_st[kWarps][32];
+    __shared__ TileInfo s_ti[kWarps];
+    __shared__ unsigned long long s_red[kWarps];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    Staged *slots = s_st[warp];
+    TileInfo &ti = s_ti[warp];
     unsigned long long evals = 0;
 
     for (;;) {
-        __syncthreads();
-        if (tid == 0) s_tile = atomicAdd(A.queue, 1u);
-        __syncthreads();
-        const int64_t tile = s_tile;
-        if (tile >= A.n_tiles) break;
-        const int v = A.tile_view[tile];
-        const ViewDesc &vd = A.views[v];
-        const int lt = static_cast<int>(tile - vd.tile_offset);
-        const int tr = lt / vd.tiles_c, tc = lt - tr * vd.tiles_c;
-        build_frame(vd, A.frames, tr, tc, tid, s_tf);
-        if (tid == 0) {
-            s_tf.view = v;
-            s_tf.tr = tr;
-            s_tf.tc = tc;
-        }
-        const int r = tr * TH + lr, c = tc * TW + lc;
-        const bool inside = r < vd.rows && c < vd.cols;
-        const Pix px = pixel_frame<TH, TW>(vd, A.frames, tr, lr, lc);
+        const uint32_t item = next_item(A.queue, lane);
+        if (item >= A.n_items) break;
+        const int64_t tile = item / kBlocksPerTile;
+        const int blk = item % kBlocksPerTile;
+        __syncwarp();
+        load_tile(A.tiles, tile, ti, lane);
+        const BlockPix bp = block_pixel<TH, TW>(ti, blk, lane);
+        const Pix px = load_pix(A.pixframes, bp.inside ? bp.pf : ti.pix_base);
         const uint2 rg = A.ranges[tile];
-        const int len = static_cast<int>(rg.y - rg.x);
         float T = 1.0f, D = 0.0f, N0 = 0.0f, N1 = 0.0f, N2 = 0.0f, O = 0.0f;
         int last = 0;
-        bool done = !inside;
-        __syncthreads();   // frame ready
+        bool done = !bp.inside;
 
-        for (int bs = 0; bs < len; bs += kBlock) {
-            if (__syncthreads_count(done ? 0 : 1) == 0) break;
-            if (bs + tid < len) {
-                const uint32_t p = A.sorted_vals[rg.x + bs + tid];
+        for (uint32_t ch = rg.x; ch < rg.y; ch += 32) {
+            if (__all_sync(0xFFFFFFFFu, done)) break;
+            const uint32_t j = ch + lane;
+            bool rel = false;
+            if (j < rg.y) {
+                const uint32_t p = A.sorted_vals[j];
                 const PairRec rec = A.recs[p];
-                Prim pr;
-                stage(A, s_tf, p, rec, local_rect<TH, TW>(rec, vd, tr, tc), s_st[tid], pr);
-            }
-            __syncthreads();
-            if (!done) {
-                const int nb = len - bs < kBlock ? len - bs : kBlock;
-                for (int k = 0; k < nb; ++k) {
-                    const Staged &s = s_st[k];
-                    if (!in_rect(__float_as_uint(s.b.w), lr, lc)) continue;
-                    ++evals;
-                    Hit h;
-                    if (!evaluate(s, px, A.sigma, A.alpha_min, A.alpha_max, h)) continue;
-                    const float tt = __fmul_rn(T, __fsub_rn(1.0f, h.a));
-                    if (tt < A.t_min) {
-                        done = true;
-                        break;
-                    }
-                    const float w = __fmul_rn(h.a, T);
-                    D = __fmaf_rn(w, h.d, D);
-                    const float4 nn = s.n;
-                    N0 = __fmaf_rn(w, nn.x, N0);
-                    N1 = __fmaf_rn(w, nn.y, N1);
-                    N2 = __fmaf_rn(w, nn.z, N2);
-                    O = __fadd_rn(O, w);
-                    T = tt;
-                    last = bs + k + 1;
+                const uint32_t rect = local_rect<TH, TW>(rec, ti);
+                rel = rect_meets_block(rect, bp.br, bp.bc);
+                if (rel) {
+                    Prim pr;
+                    stage(A, ti, p, rec, rect, slots[lane], pr);
                 }
             }
+            uint32_t m = __ballot_sync(0xFFFFFFFFu, rel);
+            __syncwarp();
+            while (m) {
+                const int b = __ffs(m) - 1;
+                m &= m - 1;
+                const Staged &s = slots[b];
+                if (done || !in_rect(__float_as_uint(s.b.w), bp.lr, bp.lc)) continue;
+                ++evals;
+                Hit h;
+                if (!evaluate(s, px, A.sigma, A.alpha_min, A.alpha_max, h)) continue;
+                const float tt = __fmul_rn(T, __fsub_rn(1.0f, h.a));
+                if (tt < A.t_min) {
+                    done = true;
+                    continue;
+                }
+                const float w = __fmul_rn(h.a, T);
+                D = __fmaf_rn(w, h.d, D);
+                const float4 nn = s.n;
+                N0 = __fmaf_rn(w, nn.x, N0);
+                N1 = __fmaf_rn(w, nn.y, N1);
+                N2 = __fmaf_rn(w, nn.z, N2);
+                O = __fadd_rn(O, w);
+                T = tt;
+                last = static_cast<int>(ch - rg.x) + b + 1;
+            }
+            __syncwarp();
         }
-        if (inside) {
-            const int64_t pix = vd.pixel_offset + static_cast<int64_t>(r) * vd.cols + c;
-            A.depth[pix] = D;
-            A.normal[pix] = N0;
-            A.normal[A.n_pixels + pix] = N1;
-            A.normal[2 * A.n_pixels + pix] = N2;
-            A.alpha[pix] = O;
-            A.t_final[pix] = T;
-            A.n_last[pix] = last;
+        if (bp.inside) {
+            A.depth[bp.out] = D;
+            A.normal[bp.out] = N0;
+            A.normal[A.n_pixels + bp.out] = N1;
+            A.normal[2 * A.n_pixels + bp.out] = N2;
+            A.alpha[bp.out] = O;
+            A.t_final[bp.out] = T;
+            A.n_last[bp.out] = last;
         }
     }
     const unsigned long long tot = block_sum_u64(evals, s_red);
-    if (tid == 0 && tot) atomicAdd(A.evals, tot);
+    if (threadIdx.x == 0 && tot) atomicAdd(A.evals, tot);
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -382,78 +400,74 @@ constexpr int kAcc = 16;   // per staged primitive: g_ba'(3) g_bb'(3) g_c'(3) g_
 template <int TH, int TW>
 __global__ void __launch_bounds__(kBlock, 2) k_render_bwd(const RenderArgs A)
 {
-    __shared__ Staged s_st[kBlock];
-    __shared__ float s_acc[kBlock][kAcc];
-    __shared__ TileFrame s_tf;
-    __shared__ int64_t s_tile;
-    __shared__ int s_maxlast;
-    __shared__ unsigned long long s_red[kBlock / 32];
-    const int tid = threadIdx.x, lane = tid & 31;
-    const int lr = tid / TW, lc = tid % TW;
+    static_assert(TH * TW == kBlock && TH % 4 == 0 && TW % 8 == 0, "4x8 warp blocks");
+    __shared__ Staged s_st[kWarps][32];
+    __shared__ float s_acc[kWarps][32][kAcc];
+    __shared__ TileInfo s_ti[kWarps];
+    __shared__ unsigned long long s_red[kWarps];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    Staged *slots = s_st[warp];
+    float(*acc)[kAcc] = s_acc[warp];
+    TileInfo &ti = s_ti[warp];
     unsigned long long evals = 0;
 
     for (;;) {
-        __syncthreads();
-        if (tid == 0) {
-            s_tile = atomicAdd(A.queue, 1u);
-            s_maxlast = 0;
-        }
-        __syncthreads();
-        const int64_t tile = s_tile;
-        if (tile >= A.n_tiles) break;
-        const int v = A.tile_view[tile];
-        const ViewDesc &vd = A.views[v];
-        const int lt = static_cast<int>(tile - vd.tile_offset);
-        const int tr = lt / vd.tiles_c, tc = lt - tr * vd.tiles_c;
-        build_frame(vd, A.frames, tr, tc, tid, s_tf);
-        if (tid == 0) {
-            s_tf.view = v;
-            s_tf.tr = tr;
-            s_tf.tc = tc;
-        }
-        const int r = tr * TH + lr, c = tc * TW + lc;
-        const bool inside = r < vd.rows && c < vd.cols;
-        const Pix px = pixel_frame<TH, TW>(vd, A.frames, tr, lr, lc);
+        const uint32_t item = next_item(A.queue, lane);
+        if (item >= A.n_items) break;
+        const int64_t tile = item / kBlocksPerTile;
+        const int blk = item % kBlocksPerTile;
+        __syncwarp();
+        load_tile(A.tiles, tile, ti, lane);
+        const BlockPix bp = block_pixel<TH, TW>(ti, blk, lane);
+        const Pix px = load_pix(A.pixframes, bp.inside ? bp.pf : ti.pix_base);
         const uint2 rg = A.ranges[tile];
         float T = 1.0f, gD = 0.0f, gN0 = 0.0f, gN1 = 0.0f, gN2 = 0.0f, gO = 0.0f;
         int nl = 0;
-        if (inside) {
-            const int64_t pix = vd.pixel_offset + static_cast<int64_t>(r) * vd.cols + c;
-            T = A.t_final[pix];
-            nl = A.n_last[pix];
-            if (A.g_depth) gD = A.g_depth[pix];
+        if (bp.inside) {
+            T = A.t_final[bp.out];
+            nl = A.n_last[bp.out];
+            if (A.g_depth) gD = A.g_depth[bp.out];
             if (A.g_normal) {
-                gN0 = A.g_normal[pix];
-                gN1 = A.g_normal[A.n_pixels + pix];
-                gN2 = A.g_normal[2 * A.n_pixels + pix];
+                gN0 = A.g_normal[bp.out];
+                gN1 = A.g_normal[A.n_pixels + bp.out];
+                gN2 = A.g_normal[2 * A.n_pixels + bp.out];
             }
-            if (A.g_alpha) gO = A.g_alpha[pix];
-            if (nl > 0) atomicMax(&s_maxlast, nl);
+            if (A.g_alpha) gO = A.g_alpha[bp.out];
         }
         float Bd = 0.0f, Bo = 0.0f, Bn0 = 0.0f, Bn1 = 0.0f, Bn2 = 0.0f;
-        __syncthreads();   // frame and s_maxlast ready
-        const int maxlast = s_maxlast;
+        // the warp's bound: nothing at or past it contributes to any of its pixels
+        int wl = nl;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) wl = max(wl, __shfl_xor_sync(0xFFFFFFFFu, wl, o));
 
-        for (int be = maxlast; be > 0; be -= kBlock) {
-            const int bs = be - kBlock > 0 ? be - kBlock : 0;
-            __syncthreads();
+        for (int ch = ((wl - 1) >> 5) << 5; ch >= 0 && wl > 0; ch -= 32) {
+            const int jl = ch + lane;   // list position of this lane's entry
+            bool rel = false;
             Prim pr;
             pr.i = -1;
-            if (bs + tid < be) {
-                const uint32_t p = A.sorted_vals[rg.x + bs + tid];
+            if (jl < wl) {
+                const uint32_t p = A.sorted_vals[rg.x + jl];
                 const PairRec rec = A.recs[p];
-                stage(A, s_tf, p, rec, local_rect<TH, TW>(rec, vd, tr, tc), s_st[tid], pr);
-            }
+                const uint32_t rect = local_rect<TH, TW>(rec, ti);
+                rel = rect_meets_block(rect, bp.br, bp.bc);
+                if (rel) {
+                    stage(A, ti, p, rec, rect, slots[lane], pr);
 #pragma unroll
-            for (int j = 0; j < kAcc; ++j) s_acc[tid][j] = 0.0f;
-            __syncthreads();
-            for (int k = be - 1; k >= bs; --k) {
-                const Staged &s = s_st[k - bs];
+                    for (int q = 0; q < kAcc; ++q) acc[lane][q] = 0.0f;
+                }
+            }
+            uint32_t m = __ballot_sync(0xFFFFFFFFu, rel);
+            __syncwarp();
+            while (m) {
+                const int b = 31 - __clz(m);
+                m &= ~(1u << b);
+                const int k = ch + b;
+                const Staged &s = slots[b];
                 float g[13];
 #pragma unroll
-                for (int j = 0; j < 13; ++j) g[j] = 0.0f;
+                for (int q = 0; q < 13; ++q) g[q] = 0.0f;
                 bool contrib = false;
-                if (k < nl && in_rect(__float_as_uint(s.b.w), lr, lc)) {
+                if (k < nl && in_rect(__float_as_uint(s.b.w), bp.lr, bp.lc)) {
                     ++evals;
                     Hit h;
                     if (evaluate(s, px, A.sigma, A.alpha_min, A.alpha_max, h)) {
@@ -508,29 +522,36 @@ __global__ void __launch_bounds__(kBlock, 2) k_render_bwd(const RenderArgs A)
                         g[8] = -rb2 * px.hx2 + ra2 * px.hy2 + gd * px.v2;
                     }
                 }
-                if (__any_sync(0xFFFFFFFFu, contrib)) {
+                const uint32_t cm = __ballot_sync(0xFFFFFFFFu, contrib);
+                if (cm == 0u) continue;
+                if (__popc(cm) <= kDirectLanes) {
+                    if (contrib) {
 #pragma unroll
-                    for (int j = 0; j < 13; ++j) {
+                        for (int q = 0; q < 13; ++q) atomicAdd(&acc[b][q], g[q]);
+                    }
+                } else {
+#pragma unroll
+                    for (int q = 0; q < 13; ++q) {
 #pragma unroll
                         for (int o = 16; o > 0; o >>= 1)
-                            g[j] += __shfl_xor_sync(0xFFFFFFFFu, g[j], o);
+                            g[q] += __shfl_xor_sync(0xFFFFFFFFu, g[q], o);
                     }
                     if (lane == 0) {
 #pragma unroll
-                        for (int j = 0; j < 13; ++j) atomicAdd(&s_acc[k - bs][j], g[j]);
+                        for (int q = 0; q < 13; ++q) acc[b][q] += g[q];
                     }
                 }
             }
-            __syncthreads();
-            if (pr.i >= 0) {
-                const float *a = s_acc[tid];
+            __syncwarp();
+            if (rel) {
+                const float *a = acc[lane];
                 bool any = false;
 #pragma unroll
-                for (int j = 0; j < 13; ++j) any |= a[j] != 0.0f;
+                for (int q = 0; q < 13; ++q) any |= a[q] != 0.0f;
                 if (any) {
-                    const float *M = s_tf.Mh;
-                    const float *R = s_tf.Rh;
-                    const Staged &s = s_st[tid];
+                    const float *M = ti.M_hi;
+                    const float *R = ti.R;
+                    const Staged &s = slots[lane];
                     // world frame: M^T g' (M = Q R^c_w), normals: R^c_w^T g_n
                     float gmu[3], gta[3], gtb[3], gtn[3];
 #pragma unroll
@@ -550,15 +571,13 @@ __global__ void __launch_bounds__(kBlock, 2) k_render_bwd(const RenderArgs A)
                     atomicAdd(dst + 3, make_float4(gtn[0], gtn[1], gtn[2], 0.0f));
                 }
             }
+            __syncwarp();
         }
     }
     const unsigned long long tot = block_sum_u64(evals, s_red);
-    if (tid == 0 && tot) atomicAdd(A.evals, tot);
+    if (threadIdx.x == 0 && tot) atomicAdd(A.evals, tot);
 }
 
-// ---------------------------------------------------------------------------------------------
-// K7: world-frame accumulators -> parameter gradients
-// ---------------------------------------------------------------------------------------------
 __global__ void k_param_grads(const float4 *__restrict__ pos_logit, const float4 *__restrict__ quat,
                               const float4 *__restrict__ wgrad, int64_t n,
                               float4 *__restrict__ g_pl, float4 *__restrict__ g_q,
