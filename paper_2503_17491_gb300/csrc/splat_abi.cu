@@ -81,6 +81,7 @@ struct splat_ctx {
     PixFrame *d_pixframes = nullptr;   // grown by splat_set_views
     int64_t pixframe_cap = 0;
     TileInfo *d_tileinfo = nullptr;
+    uint32_t *d_tile_order = nullptr;
 
     // workspace
     PairRec *d_recs = nullptr;
@@ -137,6 +138,7 @@ splat::RenderArgs render_args(splat_ctx *ctx, const splat_gaussians *g)
     a.tiles = ctx->d_tileinfo;
     a.pixframes = ctx->d_pixframes;
     a.ranges = ctx->d_ranges;
+    a.tile_order = ctx->d_tile_order;
     a.sorted_vals = ctx->sorted_vals;
     a.recs = ctx->d_recs;
     a.n_tiles = ctx->n_tiles;
@@ -178,6 +180,7 @@ int render_core(splat_ctx *ctx, const splat_gaussians *g, float *depth, float *n
                                ctx->cap.max_pairs, bits_for(ctx->n_tiles), ctx->d_hist, &tk, &tv,
                                st));
     CK(splat::launch_ranges(tk, cnt, ctx->cap.max_pairs, ctx->d_ranges, ctx->n_tiles, st));
+    CK(splat::launch_order_tiles(ctx->d_ranges, ctx->n_tiles, ctx->d_tile_order, st));
     ctx->sorted_keys = tk;
     ctx->sorted_vals = tv;
     splat::RenderArgs a = render_args(ctx, g);
@@ -193,8 +196,9 @@ int render_core(splat_ctx *ctx, const splat_gaussians *g, float *depth, float *n
         CK(cudaEventRecord(ctx->ev[1], st));
         ctx->rec_fwd = true;
     }
-    // project 1, range sort 4 x 3, emission 3, tile sort 3 per byte, ranges 1, composite 1
-    ctx->launches += 1 + 12 + 3 + 3 * (bits_for(ctx->n_tiles) / 8) + 1 + 1;
+    // project 1, range sort 4 x 3, emission 3, tile sort 3 per byte, ranges 1, order 1,
+    // composite 1
+    ctx->launches += 1 + 12 + 3 + 3 * (bits_for(ctx->n_tiles) / 8) + 1 + 1 + 1;
     ctx->rendered = true;
     ctx->last_n = n;
     return SPLAT_OK;
@@ -231,7 +235,7 @@ void free_ctx(splat_ctx *c)
                     c->d_dkeys2, c->d_dvals2, c->d_tkeys, c->d_tvals, c->d_tkeys2, c->d_tvals2,
                     c->d_block_sums, c->d_hist, c->d_ranges, c->d_tfinal, c->d_nlast, c->d_wgrad,
                     c->d_img, c->d_gimg, c->d_counters, c->d_evals, c->d_pixframes,
-                    c->d_tileinfo};
+                    c->d_tileinfo, c->d_tile_order};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     for (cudaEvent_t e : c->ev)
@@ -308,6 +312,7 @@ SPLAT_API int splat_ctx_create(const splat_render_config *cfg, const splat_capac
     if (e == cudaSuccess) e = dalloc(&c->d_frames, static_cast<size_t>(c->frame_cap) * 4);
     if (e == cudaSuccess) e = dalloc(&c->d_tile_view, TT);
     if (e == cudaSuccess) e = dalloc(&c->d_tileinfo, TT);
+    if (e == cudaSuccess) e = dalloc(&c->d_tile_order, TT);
     if (e == cudaSuccess) e = dalloc(&c->d_recs, mpv);
     if (e == cudaSuccess) e = dalloc(&c->d_dkeys, mpv);
     if (e == cudaSuccess) e = dalloc(&c->d_dvals, mpv);

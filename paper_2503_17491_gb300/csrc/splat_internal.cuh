@@ -229,6 +229,10 @@ cudaError_t launch_emit(const uint32_t *sorted_pair_ids, int64_t n_pairs_total, 
 cudaError_t launch_ranges(const uint32_t *tile_keys, const uint32_t *d_count, int64_t max_pairs,
                           uint2 *ranges, int64_t n_tiles, cudaStream_t st);
 
+// tiles ordered by decreasing log2 of their list length (order inside a bucket unspecified)
+cudaError_t launch_order_tiles(const uint2 *ranges, int64_t n_tiles, uint32_t *order,
+                               cudaStream_t st);
+
 struct RenderArgs {
     const float4 *pos_logit;
     const float4 *quat;
@@ -237,6 +241,7 @@ struct RenderArgs {
     const TileInfo *tiles;        // global tile -> frame and addressing
     const PixFrame *pixframes;
     const uint2 *ranges;          // global tile -> [start, end)
+    const uint32_t *tile_order;   // tiles in decreasing order of list length (work order)
     const uint32_t *sorted_vals;  // pair ids in (tile, range, id) order
     const PairRec *recs;
     int64_t n_tiles;

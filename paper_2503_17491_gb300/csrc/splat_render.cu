@@ -5,7 +5,7 @@
 // Work decomposition.  A work item is one 4 x 8 pixel block of one tile (a tile is
 // tile_h x tile_w = 256 pixels, i.e. 8 blocks), taken by one warp, one pixel per lane; the queue
 // holds the blocks of every tile of every registered view, so many keyframes of uneven sizes
-// share one launch.  Warps never wait for one another: each walks its tile's slice of the
+// share one launch, and hands tiles out longest list first so that the last items are short.  Warps never wait for one another: each walks its tile's slice of the
 // sorted list (Sec. 3.2.1) 32 entries at a time -- every lane reads one entry's projection
 // record, tests whether the primitive's pixel rectangle meets the warp's block, and the lanes
 // that hit stage their primitive into the warp's shared-memory slots -- then the warp evaluates
@@ -255,17 +255,12 @@ __device__ __forceinline__ bool evaluate(const Staged &s, const Pix &px, float s
     return h.d > 0.0f;
 }
 
-__device__ __forceinline__ unsigned long long block_sum_u64(unsigned long long v,
-                                                            unsigned long long *s_red)
+// add a per-lane counter to a global total: one atomic per warp, no block barrier
+__device__ __forceinline__ void warp_count(unsigned long long v, unsigned long long *total)
 {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xFFFFFFFFu, v, o);
-    if ((threadIdx.x & 31) == 0) s_red[threadIdx.x >> 5] = v;
-    __syncthreads();
-    unsigned long long t = 0;
-    if (threadIdx.x == 0)
-        for (int w = 0; w < kWarps; ++w) t += s_red[w];
-    return t;
+    if ((threadIdx.x & 31) == 0 && v) atomicAdd(total, v);
 }
 
 // the next work item of this warp (lane 0 takes it from the queue)
@@ -317,7 +312,6 @@ __global__ void __launch_bounds__(kBlock, 3) k_render_fwd(const RenderArgs A)
     static_assert(TH * TW == kBlock && TH % 4 == 0 && TW % 8 == 0, "4x8 warp blocks");
     __shared__ Staged s_st[kWarps][32];
     __shared__ TileInfo s_ti[kWarps];
-    __shared__ unsigned long long s_red[kWarps];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     Staged *slots = s_st[warp];
     TileInfo &ti = s_ti[warp];
@@ -326,7 +320,7 @@ __global__ void __launch_bounds__(kBlock, 3) k_render_fwd(const RenderArgs A)
     for (;;) {
         const uint32_t item = next_item(A.queue, lane);
         if (item >= A.n_items) break;
-        const int64_t tile = item / kBlocksPerTile;
+        const int64_t tile = A.tile_order[item / kBlocksPerTile];
         const int blk = item % kBlocksPerTile;
         __syncwarp();
         load_tile(A.tiles, tile, ti, lane);
@@ -388,8 +382,7 @@ __global__ void __launch_bounds__(kBlock, 3) k_render_fwd(const RenderArgs A)
             A.n_last[bp.out] = last;
         }
     }
-    const unsigned long long tot = block_sum_u64(evals, s_red);
-    if (threadIdx.x == 0 && tot) atomicAdd(A.evals, tot);
+    warp_count(evals, A.evals);
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -398,13 +391,12 @@ __global__ void __launch_bounds__(kBlock, 3) k_render_fwd(const RenderArgs A)
 constexpr int kAcc = 16;   // per staged primitive: g_ba'(3) g_bb'(3) g_c'(3) g_n(3) g_o, pad
 
 template <int TH, int TW>
-__global__ void __launch_bounds__(kBlock, 2) k_render_bwd(const RenderArgs A)
+__global__ void __launch_bounds__(kBlock, 3) k_render_bwd(const RenderArgs A)
 {
     static_assert(TH * TW == kBlock && TH % 4 == 0 && TW % 8 == 0, "4x8 warp blocks");
     __shared__ Staged s_st[kWarps][32];
     __shared__ float s_acc[kWarps][32][kAcc];
     __shared__ TileInfo s_ti[kWarps];
-    __shared__ unsigned long long s_red[kWarps];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     Staged *slots = s_st[warp];
     float(*acc)[kAcc] = s_acc[warp];
@@ -414,7 +406,7 @@ __global__ void __launch_bounds__(kBlock, 2) k_render_bwd(const RenderArgs A)
     for (;;) {
         const uint32_t item = next_item(A.queue, lane);
         if (item >= A.n_items) break;
-        const int64_t tile = item / kBlocksPerTile;
+        const int64_t tile = A.tile_order[item / kBlocksPerTile];
         const int blk = item % kBlocksPerTile;
         __syncwarp();
         load_tile(A.tiles, tile, ti, lane);
@@ -574,8 +566,7 @@ __global__ void __launch_bounds__(kBlock, 2) k_render_bwd(const RenderArgs A)
             __syncwarp();
         }
     }
-    const unsigned long long tot = block_sum_u64(evals, s_red);
-    if (threadIdx.x == 0 && tot) atomicAdd(A.evals, tot);
+    warp_count(evals, A.evals);
 }
 
 __global__ void k_param_grads(const float4 *__restrict__ pos_logit, const float4 *__restrict__ quat,

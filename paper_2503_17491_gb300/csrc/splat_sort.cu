@@ -286,7 +286,45 @@ __global__ void k_ranges(const uint32_t *__restrict__ keys, const uint32_t *d_co
     }
 }
 
+// work order of the compositing kernels: longest lists first, by log2 of the length, so that
+// the persistent queue ends on short items (one CTA; a few microseconds)
+__global__ void __launch_bounds__(1024) k_order_tiles(const uint2 *__restrict__ ranges,
+                                                      int64_t n_tiles, uint32_t *__restrict__ order)
+{
+    __shared__ uint32_t s_cnt[33], s_off[33];
+    const int tid = threadIdx.x;
+    if (tid < 33) s_cnt[tid] = 0;
+    __syncthreads();
+    for (int64_t t = tid; t < n_tiles; t += blockDim.x) {
+        const uint2 r = ranges[t];
+        const uint32_t len = r.y - r.x;
+        atomicAdd(&s_cnt[len ? 32 - __clz(len) : 0], 1u);
+    }
+    __syncthreads();
+    if (tid == 0) {
+        uint32_t run = 0;
+        for (int b = 32; b >= 0; --b) {
+            s_off[b] = run;
+            run += s_cnt[b];
+        }
+    }
+    __syncthreads();
+    for (int64_t t = tid; t < n_tiles; t += blockDim.x) {
+        const uint2 r = ranges[t];
+        const uint32_t len = r.y - r.x;
+        order[atomicAdd(&s_off[len ? 32 - __clz(len) : 0], 1u)] = static_cast<uint32_t>(t);
+    }
+}
+
 }  // namespace
+
+cudaError_t launch_order_tiles(const uint2 *ranges, int64_t n_tiles, uint32_t *order,
+                               cudaStream_t st)
+{
+    if (n_tiles <= 0) return cudaSuccess;
+    k_order_tiles<<<1, 1024, 0, st>>>(ranges, n_tiles, order);
+    return cudaGetLastError();
+}
 
 cudaError_t radix_sort_pairs(uint32_t *keys, uint32_t *vals, uint32_t *keys_alt, uint32_t *vals_alt,
                              const uint32_t *d_count, int64_t max_n, int bits, uint32_t *tmp_hist,
