@@ -230,6 +230,28 @@ SPLAT_API int splat_refine_step(splat_ctx *ctx, float *pos_logit, float *quat, f
                                 float *v_quat, float *v_log_scale, int32_t *step,
                                 double *loss_out, void *stream);
 
+/* ---- rendering without allocation -------------------------------------------------------- */
+
+/* The paper has no counterpart to this entry point: it exists for callers that cannot allocate
+ * device memory (for instance a process whose device memory is owned by another allocator, or
+ * code that must not call cudaMalloc once it is running).  It renders one view like
+ * splat_render, with no context: every workspace buffer lives in one array of the library
+ * (about 7 MB, held on every device that loads the library until the process exits), and the
+ * call allocates nothing -- no cudaMalloc, cudaFree or host heap.
+ * Limits: g->n <= 16384 primitives, rows <= 256, rows * cols <= 65536 pixels, at most 4096
+ * tiles and 262144 (tile, primitive) pairs.  cfg = NULL uses splat_default_config.
+ * Outputs: depth[P], normal[3][P], alpha[P] (P = rows * cols), as splat_render.
+ * The call waits for its stream before returning.  Errors: INVALID_ARG (null pointer or a size
+ * beyond the limits, bad pose or intrinsics), UNSUPPORTED (tile shape), CAPACITY (more pairs
+ * than the limit: outputs invalid), NONFINITE (a primitive had a non-finite value: it was
+ * skipped), CUDA.  All calls share the one array, which keeps the previous call's contents:
+ * calls that overlap on the GPU, or come from several host threads at once, race.  The first
+ * call on each device looks up the array's device address, with that device current. */
+SPLAT_API int splat_render_noalloc(const splat_gaussians *g, const double T_world_sensor[16],
+                                   const splat_lidar_intrinsics *intr,
+                                   const splat_render_config *cfg, float *depth, float *normal,
+                                   float *alpha, void *stream);
+
 /* ---- status, statistics, inspection ------------------------------------------------------- */
 
 /* Synchronise the device and read (then clear) the status word. */

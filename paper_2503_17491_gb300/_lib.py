@@ -86,6 +86,9 @@ SIGNATURES = {
     "splat_get_stats": ([_P, ctypes.POINTER(splat_stats)], _I),
     "splat_debug_copy": ([_P, _I32, _P, _I64], _I64),
     "splat_set_profiling": ([_P, _I], _I),
+    "splat_render_noalloc": ([ctypes.POINTER(splat_gaussians), _P,
+                              ctypes.POINTER(splat_lidar_intrinsics),
+                              ctypes.POINTER(splat_render_config), _P, _P, _P, _P], _I),
     "splat_kernel_times": ([_P, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_float)],
                            _I),
 }

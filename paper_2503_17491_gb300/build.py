@@ -28,6 +28,7 @@ UNITS = {
     "splat_render.cu": [],
     "splat_optim.cu": [],
     "splat_abi.cu": [],
+    "splat_noalloc.cu": [],
 }
 
 
