@@ -44,6 +44,10 @@ def parse():
     p.add_argument("--warmup", type=int, default=5)
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
     p.add_argument("--workload", type=int, default=3)
+    p.add_argument("--n-gaussians", type=int, default=None,
+                   help="override the workload's primitive count (smaller profiling cases)")
+    p.add_argument("--keyframes", type=int, default=None,
+                   help="use only the first K keyframes of the workload")
     p.add_argument("--tile", default="auto", help="auto | 16x16 | 8x32 | 32x8 | 4x64")
     p.add_argument("--plain-steps", type=int, default=10)
     p.add_argument("--e2e-steps", type=int, default=50)
@@ -152,14 +156,18 @@ class ClockSampler:
 # workload
 # ----------------------------------------------------------------------------------------------
 
-def build_workload(index):
+def build_workload(index, n=None, keyframes=None):
     from paper_2503_17491_gb300 import scenes
-    s = scenes.workload(index)
+    s = scenes.workload(index, n=n)
     views = s.views
     if index == 4:
         views = views[:8]   # the 8 most recent keyframes of the long run's first window
+    if keyframes:
+        views = views[:keyframes]
     targets = [scenes.render_targets(s, v) for v in views]
     desc = scenes.WORKLOADS[index]
+    if n or keyframes:
+        desc += f" [reduced: {s.n} primitives, {len(views)} keyframes]"
     return s, views, targets, desc
 
 
@@ -226,7 +234,8 @@ def run_ours(args):
     dev = torch.device("cuda", local)
     libbuild.build()
 
-    scene, views, targets_np, desc = build_workload(args.workload)
+    scene, views, targets_np, desc = build_workload(args.workload, args.n_gaussians,
+                                                    args.keyframes)
     pixels = sum(v.rows * v.cols for v in views)
     params0 = [torch.from_numpy(a).to(dev) for a in (scene.pos_logit, scene.quat,
                                                       scene.log_scale)]
@@ -402,7 +411,8 @@ def run_reference(args):
     rank, world, _ = dist_info()
     if rank != 0:
         return None
-    scene, views, targets_np, desc = build_workload(args.workload)
+    scene, views, targets_np, desc = build_workload(args.workload, args.n_gaussians,
+                                                    args.keyframes)
     K, W = args.steps, args.warmup
     budget = 150.0
     per_step = max(0.05, budget / max(K + W, 1))

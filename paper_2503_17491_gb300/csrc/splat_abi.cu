@@ -323,7 +323,7 @@ SPLAT_API int splat_ctx_create(const splat_render_config *cfg, const splat_capac
     if (e == cudaSuccess) e = dalloc(&c->d_tkeys2, M);
     if (e == cudaSuccess) e = dalloc(&c->d_tvals2, M);
     if (e == cudaSuccess) e = dalloc(&c->d_block_sums, splat::kScanGrid);
-    if (e == cudaSuccess) e = dalloc(&c->d_hist, static_cast<size_t>(splat::kSortGrid) * 256);
+    if (e == cudaSuccess) e = dalloc(&c->d_hist, static_cast<size_t>(splat::kHistWords));
     if (e == cudaSuccess) e = dalloc(&c->d_ranges, TT);
     if (e == cudaSuccess) e = dalloc(&c->d_tfinal, P);
     if (e == cudaSuccess) e = dalloc(&c->d_nlast, P);

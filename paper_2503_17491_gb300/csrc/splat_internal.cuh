@@ -212,9 +212,10 @@ cudaError_t launch_project(const float4 *pos_logit, const float4 *quat, const fl
 
 // stable LSD radix sort of (uint32 key, uint32 value) pairs on key bits [0, bits);
 // the count is read on the device from *d_count (clamped to max_n); result lands in
-// (keys_out, vals_out).  tmp_hist holds kSortGrid * 256 uint32.
+// (keys_out, vals_out).  tmp_hist holds kHistWords uint32.
 constexpr int kSortGrid = 304;
 constexpr int kSortTile = 2048;   // keys per CTA tile (256 threads x 8)
+constexpr int kHistWords = kSortGrid * 256 + 256;   // per-CTA digit counts + digit totals
 cudaError_t radix_sort_pairs(uint32_t *keys, uint32_t *vals, uint32_t *keys_alt, uint32_t *vals_alt,
                              const uint32_t *d_count, int64_t max_n, int bits, uint32_t *tmp_hist,
                              uint32_t **keys_out, uint32_t **vals_out, cudaStream_t st);

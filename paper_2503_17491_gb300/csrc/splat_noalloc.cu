@@ -50,7 +50,7 @@ constexpr size_t kOffTkeys2 = align256(kOffTvals + 4 * kMaxPairs);
 constexpr size_t kOffTvals2 = align256(kOffTkeys2 + 4 * kMaxPairs);
 constexpr size_t kOffBlockSums = align256(kOffTvals2 + 4 * kMaxPairs);
 constexpr size_t kOffHist = align256(kOffBlockSums + 4 * splat::kScanGrid);
-constexpr size_t kOffRanges = align256(kOffHist + 4 * size_t{splat::kSortGrid} * 256);
+constexpr size_t kOffRanges = align256(kOffHist + 4 * size_t{splat::kHistWords});
 constexpr size_t kOffOrder = align256(kOffRanges + 8 * size_t{kMaxTiles});
 constexpr size_t kOffTiles = align256(kOffOrder + 4 * size_t{kMaxTiles});
 constexpr size_t kOffPix = align256(kOffTiles + sizeof(TileInfo) * kMaxTiles);

@@ -59,36 +59,35 @@ __global__ void __launch_bounds__(kThreads) k_upsweep(const uint32_t *__restrict
     hist[static_cast<int64_t>(tid) * gridDim.x + blockIdx.x] = t;
 }
 
-// exclusive scan of hist (kRadix * grid entries), one CTA of 1024 threads
-__global__ void __launch_bounds__(1024) k_scan_hist(uint32_t *__restrict__ hist, int total)
+// per digit (one warp each): exclusive scan of its per-CTA counts hist[d * grid + b] in place,
+// and the digit's total into dtot[d]
+__global__ void __launch_bounds__(256) k_scan_digits(uint32_t *__restrict__ hist, int grid,
+                                                     uint32_t *__restrict__ dtot)
 {
-    __shared__ uint32_t s_part[1024];
-    const int tid = threadIdx.x;
-    const int per = (total + 1023) / 1024;
-    const int b = tid * per;
-    const int e = b + per < total ? b + per : total;
-    uint32_t sum = 0;
-    for (int k = b; k < e; ++k) sum += hist[k];
-    s_part[tid] = sum;
-    __syncthreads();
-    for (int off = 1; off < 1024; off <<= 1) {
-        uint32_t v = tid >= off ? s_part[tid - off] : 0u;
-        __syncthreads();
-        s_part[tid] += v;
-        __syncthreads();
+    const int lane = threadIdx.x & 31;
+    const int d = blockIdx.x * 8 + (threadIdx.x >> 5);
+    if (d >= kRadix) return;
+    uint32_t *h = hist + static_cast<int64_t>(d) * grid;
+    uint32_t carry = 0;
+    for (int b0 = 0; b0 < grid; b0 += 32) {
+        const int b = b0 + lane;
+        const uint32_t v = b < grid ? h[b] : 0u;
+        uint32_t x = v;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, x, o);
+            if (lane >= o) x += y;
+        }
+        if (b < grid) h[b] = carry + x - v;
+        carry += __shfl_sync(0xFFFFFFFFu, x, 31);
     }
-    uint32_t run = s_part[tid] - sum;
-    for (int k = b; k < e; ++k) {
-        uint32_t v = hist[k];
-        hist[k] = run;
-        run += v;
-    }
+    if (lane == 0) dtot[d] = carry;
 }
 
 __global__ void __launch_bounds__(kThreads) k_downsweep(
     const uint32_t *__restrict__ keys_in, const uint32_t *__restrict__ vals_in,
     uint32_t *__restrict__ keys_out, uint32_t *__restrict__ vals_out, const uint32_t *d_count,
-    int64_t max_n, int shift, const uint32_t *__restrict__ hist)
+    int64_t max_n, int shift, const uint32_t *__restrict__ hist, const uint32_t *__restrict__ dtot)
 {
     __shared__ uint32_t s_base[kRadix];          // running global offset per digit
     __shared__ uint32_t s_wcnt[kWarps][kRadix];  // per-warp digit counts -> warp prefixes
@@ -99,7 +98,21 @@ __global__ void __launch_bounds__(kThreads) k_downsweep(
     const int64_t begin = chunk * blockIdx.x;
     const int64_t end = begin + chunk < n ? begin + chunk : n;
     if (begin >= end) return;
-    s_base[tid] = hist[static_cast<int64_t>(tid) * gridDim.x + blockIdx.x];
+    {   // digit base: exclusive scan of the digit totals, plus this CTA's offset in its digit
+        const uint32_t t = dtot[tid];
+        uint32_t x = t;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, x, o);
+            if (lane >= o) x += y;
+        }
+        if (lane == 31) s_tile[warp] = x;
+        __syncthreads();
+        uint32_t wbase = 0;
+        for (int w = 0; w < warp; ++w) wbase += s_tile[w];
+        s_base[tid] = wbase + x - t + hist[static_cast<int64_t>(tid) * gridDim.x + blockIdx.x];
+        __syncthreads();
+    }
     const uint32_t lt_mask = (1u << lane) - 1u;
 
     for (int64_t tb = begin; tb < end; tb += kSortTile) {
@@ -333,10 +346,11 @@ cudaError_t radix_sort_pairs(uint32_t *keys, uint32_t *vals, uint32_t *keys_alt,
     uint32_t *kin = keys, *vin = vals, *kout = keys_alt, *vout = vals_alt;
     if (max_n > 0) {
         for (int shift = 0; shift < bits; shift += 8) {
+            uint32_t *dtot = tmp_hist + kSortGrid * kRadix;
             k_upsweep<<<kSortGrid, kThreads, 0, st>>>(kin, d_count, max_n, shift, tmp_hist);
-            k_scan_hist<<<1, 1024, 0, st>>>(tmp_hist, kSortGrid * kRadix);
+            k_scan_digits<<<kRadix / 8, 256, 0, st>>>(tmp_hist, kSortGrid, dtot);
             k_downsweep<<<kSortGrid, kThreads, 0, st>>>(kin, vin, kout, vout, d_count, max_n, shift,
-                                                        tmp_hist);
+                                                        tmp_hist, dtot);
             uint32_t *t = kin;
             kin = kout;
             kout = t;
