@@ -33,7 +33,8 @@
 // backward replays exactly the contributor set of the forward.  The backward recovers
 // T_k = T_{k+1} / (1 - alpha_k) from the final transmittance, keeps the suffix sums B_{d,k},
 // B_{n,k}, B_{o,k} of Supp. D.2, sums each primitive's 13 per-pixel terms over the warp (a
-// shuffle tree, or direct shared-memory atomics when only a few lanes contribute) into the
+// recursive-halving reduce-scatter, or direct shared-memory atomics when only a few lanes
+// contribute) into the
 // primitive's slot, and the lane that staged the primitive rotates the slot back to the world
 // frame and issues four float4 atomics into a per-primitive accumulator (view independent, so
 // gradients of many views add up directly).
@@ -44,7 +45,7 @@ namespace splat {
 namespace {
 
 constexpr float kLooseBox = 1.01f;   // margin of the binary32 pre-test
-constexpr int kDirectLanes = 6;      // up to this many contributing lanes: direct smem atomics
+constexpr int kDirectLanes = 3;      // up to this many contributing lanes: direct smem atomics
 constexpr int kWarps = kBlock / 32;  // warps per CTA (independent)
 constexpr int kBlocksPerTile = kBlock / 32;
 
@@ -239,7 +240,7 @@ __device__ __forceinline__ bool evaluate(const Staged &s, const Pix &px, float s
     h.px = __fmaf_rn(h.ha1, h.hb2, -__fmul_rn(h.ha2, h.hb1));
     h.py = __fmaf_rn(h.ha2, h.hb0, -__fmul_rn(h.ha0, h.hb2));
     if (!(fmaxf(fabsf(h.px), fabsf(h.py)) <= __fmul_rn(sigma, apz))) return false;
-    h.inv = __frcp_rn(h.pz);
+    h.inv = __fdividef(1.0f, h.pz);
     h.sa = __fmul_rn(h.px, h.inv);
     h.sb = __fmul_rn(h.py, h.inv);
     const float r2 = __fmaf_rn(h.sa, h.sa, __fmul_rn(h.sb, h.sb));
@@ -253,6 +254,32 @@ __device__ __forceinline__ bool evaluate(const Staged &s, const Pix &px, float s
     const float nu2 = __fmaf_rn(h.sa, s.a.z, __fmaf_rn(h.sb, s.b.z, s.c.z));
     h.d = dot3e(nu0, nu1, nu2, px.v0, px.v1, px.v2);
     return h.d > 0.0f;
+}
+
+// Sum 16 per-lane values over the warp by recursive halving (a reduce-scatter): at each of 4
+// exchange steps a lane keeps half of its values and adds its partner's copy of that half, then
+// a fifth exchange completes the 32-lane sum.  Returns the total of value index
+// reduced_index(lane) -- 16 shuffles instead of 80 for a shuffle tree per value.
+__device__ __forceinline__ float warp_reduce16(float (&v)[16], int lane)
+{
+#pragma unroll
+    for (int s = 0; s < 4; ++s) {
+        const int m = 1 << s;
+        const int half = 8 >> s;
+        const bool up = (lane & m) != 0;
+#pragma unroll
+        for (int k = 0; k < half; ++k) {
+            const float send = up ? v[k] : v[k + half];
+            const float keep = up ? v[k + half] : v[k];
+            v[k] = keep + __shfl_xor_sync(0xFFFFFFFFu, send, m);
+        }
+    }
+    return v[0] + __shfl_xor_sync(0xFFFFFFFFu, v[0], 16);
+}
+
+__device__ __forceinline__ int reduced_index(int lane)
+{
+    return ((lane & 1) ? 8 : 0) + ((lane & 2) ? 4 : 0) + ((lane & 4) ? 2 : 0) + ((lane & 8) ? 1 : 0);
 }
 
 // add a per-lane counter to a global total: one atomic per warp, no block barrier
@@ -455,9 +482,9 @@ __global__ void __launch_bounds__(kBlock, 3) k_render_bwd(const RenderArgs A)
                 m &= ~(1u << b);
                 const int k = ch + b;
                 const Staged &s = slots[b];
-                float g[13];
+                float g[16];
 #pragma unroll
-                for (int q = 0; q < 13; ++q) g[q] = 0.0f;
+                for (int q = 0; q < 16; ++q) g[q] = 0.0f;
                 bool contrib = false;
                 if (k < nl && in_rect(__float_as_uint(s.b.w), bp.lr, bp.lc)) {
                     ++evals;
@@ -465,9 +492,9 @@ __global__ void __launch_bounds__(kBlock, 3) k_render_bwd(const RenderArgs A)
                     if (evaluate(s, px, A.sigma, A.alpha_min, A.alpha_max, h)) {
                         contrib = true;
                         const float om = __fsub_rn(1.0f, h.a);
-                        const float Tk = __fdiv_rn(T, om);
+                        const float inv_om = __fdividef(1.0f, om);
+                        const float Tk = T * inv_om;
                         const float w = __fmul_rn(h.a, Tk);
-                        const float inv_om = __frcp_rn(om);
                         const float4 nn = s.n;
                         // dL/dalpha_k = sum_ch g_ch (x_k A_k - B_ch,k / (1 - alpha_k))
                         float gA = gD * (h.d * Tk - Bd * inv_om);
@@ -522,16 +549,9 @@ __global__ void __launch_bounds__(kBlock, 3) k_render_bwd(const RenderArgs A)
                         for (int q = 0; q < 13; ++q) atomicAdd(&acc[b][q], g[q]);
                     }
                 } else {
-#pragma unroll
-                    for (int q = 0; q < 13; ++q) {
-#pragma unroll
-                        for (int o = 16; o > 0; o >>= 1)
-                            g[q] += __shfl_xor_sync(0xFFFFFFFFu, g[q], o);
-                    }
-                    if (lane == 0) {
-#pragma unroll
-                        for (int q = 0; q < 13; ++q) acc[b][q] += g[q];
-                    }
+                    const float tot = warp_reduce16(g, lane);
+                    const int q = reduced_index(lane);
+                    if (lane < 16 && q < 13) acc[b][q] += tot;
                 }
             }
             __syncwarp();
