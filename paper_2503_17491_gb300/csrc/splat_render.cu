@@ -10,7 +10,8 @@
 // record, tests whether the primitive's pixel rectangle meets the warp's block, and the lanes
 // that hit stage their primitive into the warp's shared-memory slots -- then the warp evaluates
 // only the staged primitives, in list order (front to back in the forward, back to front in the
-// backward).  A warp leaves its block as soon as all its pixels are saturated.
+// backward); the entries that meet the block are queued and staged 32 at a time.  A warp leaves
+// its block as soon as all its pixels are saturated.
 //
 // Numerics.  Each pixel ray is intersected with a splat as two planes h_x, h_y through the
 // sensor (Sec. 3.2.2, Eq. planes_to_splat; Supp. D.1): h_a = (h_x.b_a, h_x.b_b, h_x.b_c),
@@ -33,8 +34,7 @@
 // backward replays exactly the contributor set of the forward.  The backward recovers
 // T_k = T_{k+1} / (1 - alpha_k) from the final transmittance, keeps the suffix sums B_{d,k},
 // B_{n,k}, B_{o,k} of Supp. D.2, sums each primitive's 13 per-pixel terms over the warp (a
-// recursive-halving reduce-scatter, or direct shared-memory atomics when only a few lanes
-// contribute) into the
+// recursive-halving reduce-scatter; shared-memory atomics measured twice as slow) into the
 // primitive's slot, and the lane that staged the primitive rotates the slot back to the world
 // frame and issues four float4 atomics into a per-primitive accumulator (view independent, so
 // gradients of many views add up directly).
@@ -45,7 +45,6 @@ namespace splat {
 namespace {
 
 constexpr float kLooseBox = 1.01f;   // margin of the binary32 pre-test
-constexpr int kDirectLanes = 3;      // up to this many contributing lanes: direct smem atomics
 constexpr int kWarps = kBlock / 32;  // warps per CTA (independent)
 constexpr int kBlocksPerTile = kBlock / 32;
 
@@ -70,25 +69,25 @@ __device__ __forceinline__ float dot3e(float a0, float a1, float a2, float b0, f
     return __fmaf_rn(a0, b0, __fmaf_rn(a1, b1, __fmul_rn(a2, b2)));
 }
 
-// h . c with h and c as float pairs, rounded once at the end: the products are formed exactly
-// (two-product), the two largest -- which cancel -- are summed exactly (two-sum).
+// h . c with h and c as float pairs, rounded once at the end.  In the tile frame the first two
+// products are the large ones (range x pixel offset, and the centre's lateral offset) and they
+// cancel, so they are formed exactly (two-product) and summed exactly (two-sum) with their
+// low-order cross terms; the third product (sin theta0 sin dgamma times the vertical offset) is
+// small and taken in binary32.
 __device__ __forceinline__ float dot3_f2(float h0, float h1, float h2, float l0, float l1,
-                                         float l2, const float4 &c, const float4 &cl)
+                                         const float4 &c, const float4 &cl)
 {
     const float p0 = __fmul_rn(h0, c.x), e0 = __fmaf_rn(h0, c.x, -p0);
     const float p1 = __fmul_rn(h1, c.y), e1 = __fmaf_rn(h1, c.y, -p1);
-    const float p2 = __fmul_rn(h2, c.z), e2 = __fmaf_rn(h2, c.z, -p2);
-    float s, t, s2, t2;
+    float s, t;
     two_sum(p0, p1, s, t);
-    two_sum(s, p2, s2, t2);
-    float err = __fadd_rn(__fadd_rn(e0, e1), __fadd_rn(e2, __fadd_rn(t, t2)));
+    float err = __fadd_rn(__fadd_rn(e0, e1), t);
     err = __fmaf_rn(h0, cl.x, err);
     err = __fmaf_rn(h1, cl.y, err);
-    err = __fmaf_rn(h2, cl.z, err);
     err = __fmaf_rn(l0, c.x, err);
     err = __fmaf_rn(l1, c.y, err);
-    err = __fmaf_rn(l2, c.z, err);
-    return __fadd_rn(s2, err);
+    err = __fmaf_rn(h2, c.z, err);
+    return __fadd_rn(s, err);
 }
 
 __device__ __forceinline__ Pix load_pix(const PixFrame *table, int index)
@@ -168,7 +167,7 @@ struct Prim {
 
 // stage pair id p of the tile into the tile frame
 __device__ __forceinline__ void stage(const RenderArgs &A, const TileInfo &ti, uint32_t p,
-                                      const PairRec &rec, uint32_t rect, Staged &out, Prim &pr)
+                                      bool flip, uint32_t rect, Staged &out, Prim &pr)
 {
     const int64_t i = static_cast<int64_t>(p) - static_cast<int64_t>(ti.view) * A.n;
     const float4 pl = A.pos_logit[i];
@@ -201,14 +200,14 @@ __device__ __forceinline__ void stage(const RenderArgs &A, const TileInfo &ti, u
     out.c = make_float4(c[0].h, c[1].h, c[2].h, 0.0f);
     out.lo = make_float4(c[0].l, c[1].l, c[2].l, 0.0f);
     const float *R = ti.R;
-    const float fs = (rec.cf & kPairFlip) ? -1.0f : 1.0f;
+    const float fs = flip ? -1.0f : 1.0f;
     out.n = make_float4(fs * (R[0] * tn0 + R[1] * tn1 + R[2] * tn2),
                         fs * (R[3] * tn0 + R[4] * tn1 + R[5] * tn2),
                         fs * (R[6] * tn0 + R[7] * tn1 + R[8] * tn2), 0.0f);
     pr.i = i;
     pr.sa = sa;
     pr.sb = sb;
-    pr.flip = (rec.cf & kPairFlip) != 0;
+    pr.flip = flip;
 }
 
 struct Hit {
@@ -235,8 +234,8 @@ __device__ __forceinline__ bool evaluate(const Staged &s, const Pix &px, float s
         !(fmaxf(fabsf(pxx), fabsf(pyy)) <= __fmul_rn(sigma * kLooseBox, apz)))
         return false;
     // precise lateral offsets of the centre from the two pixel planes
-    h.ha2 = dot3_f2(px.hx0, px.hx1, px.hx2, px.hxl0, px.hxl1, px.hxl2, s.c, s.lo);
-    h.hb2 = dot3_f2(px.hy0, px.hy1, px.hy2, px.hyl0, px.hyl1, px.hyl2, s.c, s.lo);
+    h.ha2 = dot3_f2(px.hx0, px.hx1, px.hx2, px.hxl0, px.hxl1, s.c, s.lo);
+    h.hb2 = dot3_f2(px.hy0, px.hy1, px.hy2, px.hyl0, px.hyl1, s.c, s.lo);
     h.px = __fmaf_rn(h.ha1, h.hb2, -__fmul_rn(h.ha2, h.hb1));
     h.py = __fmaf_rn(h.ha2, h.hb0, -__fmul_rn(h.ha0, h.hb2));
     if (!(fmaxf(fabsf(h.px), fabsf(h.py)) <= __fmul_rn(sigma, apz))) return false;
@@ -333,15 +332,43 @@ __device__ __forceinline__ BlockPix block_pixel(const TileInfo &ti, int blk, int
 // ---------------------------------------------------------------------------------------------
 // forward
 // ---------------------------------------------------------------------------------------------
+// Per-warp queue of list entries relevant to the warp's block: entries are appended in list
+// order 32 at a time (one chunk per step) and staged 32 at a time, so one staging pass serves 32
+// primitives whatever the fraction of the list that meets the block.
+struct WarpQueue {
+    uint32_t p[64];      // pair id
+    uint32_t rect[64];   // pixel rectangle inside the tile
+    uint32_t pos[64];    // list position, bit 31: normal flipped
+};
+
+// read one chunk entry per lane: pair id, rectangle, whether it meets the block
+template <int TH, int TW>
+__device__ __forceinline__ bool read_entry(const RenderArgs &A, const TileInfo &ti, uint32_t j,
+                                           const BlockPix &bp, uint32_t &p, uint32_t &rect,
+                                           bool &flip)
+{
+    p = A.sorted_vals[j];
+    const PairRec rec = A.recs[p];
+    rect = local_rect<TH, TW>(rec, ti);
+    flip = (rec.cf & kPairFlip) != 0;
+    return rect_meets_block(rect, bp.br, bp.bc);
+}
+
+// ---------------------------------------------------------------------------------------------
+// forward
+// ---------------------------------------------------------------------------------------------
 template <int TH, int TW>
 __global__ void __launch_bounds__(kBlock, 3) k_render_fwd(const RenderArgs A)
 {
     static_assert(TH * TW == kBlock && TH % 4 == 0 && TW % 8 == 0, "4x8 warp blocks");
     __shared__ Staged s_st[kWarps][32];
     __shared__ TileInfo s_ti[kWarps];
+    __shared__ WarpQueue s_q[kWarps];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const uint32_t lt_mask = (1u << lane) - 1u;
     Staged *slots = s_st[warp];
     TileInfo &ti = s_ti[warp];
+    WarpQueue &q = s_q[warp];
     unsigned long long evals = 0;
 
     for (;;) {
@@ -358,25 +385,14 @@ __global__ void __launch_bounds__(kBlock, 3) k_render_fwd(const RenderArgs A)
         int last = 0;
         bool done = !bp.inside;
 
-        for (uint32_t ch = rg.x; ch < rg.y; ch += 32) {
-            if (__all_sync(0xFFFFFFFFu, done)) break;
-            const uint32_t j = ch + lane;
-            bool rel = false;
-            if (j < rg.y) {
-                const uint32_t p = A.sorted_vals[j];
-                const PairRec rec = A.recs[p];
-                const uint32_t rect = local_rect<TH, TW>(rec, ti);
-                rel = rect_meets_block(rect, bp.br, bp.bc);
-                if (rel) {
-                    Prim pr;
-                    stage(A, ti, p, rec, rect, slots[lane], pr);
-                }
+        // stage queue entries [0, cnt) and composite them in list order
+        auto composite = [&](int cnt) {
+            if (lane < cnt) {
+                Prim pr;
+                stage(A, ti, q.p[lane], (q.pos[lane] >> 31) != 0, q.rect[lane], slots[lane], pr);
             }
-            uint32_t m = __ballot_sync(0xFFFFFFFFu, rel);
             __syncwarp();
-            while (m) {
-                const int b = __ffs(m) - 1;
-                m &= m - 1;
+            for (int b = 0; b < cnt; ++b) {
                 const Staged &s = slots[b];
                 if (done || !in_rect(__float_as_uint(s.b.w), bp.lr, bp.lc)) continue;
                 ++evals;
@@ -395,10 +411,39 @@ __global__ void __launch_bounds__(kBlock, 3) k_render_fwd(const RenderArgs A)
                 N2 = __fmaf_rn(w, nn.z, N2);
                 O = __fadd_rn(O, w);
                 T = tt;
-                last = static_cast<int>(ch - rg.x) + b + 1;
+                last = static_cast<int>(q.pos[b] & 0x7FFFFFFFu) + 1;
             }
             __syncwarp();
+        };
+
+        int qn = 0;
+        for (uint32_t ch = rg.x; ch < rg.y; ch += 32) {
+            if (__all_sync(0xFFFFFFFFu, done)) break;
+            const uint32_t j = ch + lane;
+            bool rel = false, flip = false;
+            uint32_t p = 0, rect = 0;
+            if (j < rg.y) rel = read_entry<TH, TW>(A, ti, j, bp, p, rect, flip);
+            const uint32_t m = __ballot_sync(0xFFFFFFFFu, rel);
+            if (rel) {
+                const int pos = qn + __popc(m & lt_mask);
+                q.p[pos] = p;
+                q.rect[pos] = rect;
+                q.pos[pos] = (j - rg.x) | (flip ? 0x80000000u : 0u);
+            }
+            qn += __popc(m);
+            __syncwarp();
+            if (qn >= 32) {
+                composite(32);
+                if (lane < qn - 32) {
+                    q.p[lane] = q.p[32 + lane];
+                    q.rect[lane] = q.rect[32 + lane];
+                    q.pos[lane] = q.pos[32 + lane];
+                }
+                qn -= 32;
+                __syncwarp();
+            }
         }
+        if (qn > 0 && !__all_sync(0xFFFFFFFFu, done)) composite(qn);
         if (bp.inside) {
             A.depth[bp.out] = D;
             A.normal[bp.out] = N0;
@@ -424,10 +469,13 @@ __global__ void __launch_bounds__(kBlock, 3) k_render_bwd(const RenderArgs A)
     __shared__ Staged s_st[kWarps][32];
     __shared__ float s_acc[kWarps][32][kAcc];
     __shared__ TileInfo s_ti[kWarps];
+    __shared__ WarpQueue s_q[kWarps];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const uint32_t gt_mask = ~((2u << lane) - 1u);   // lanes above this one
     Staged *slots = s_st[warp];
     float(*acc)[kAcc] = s_acc[warp];
     TileInfo &ti = s_ti[warp];
+    WarpQueue &q = s_q[warp];
     unsigned long long evals = 0;
 
     for (;;) {
@@ -459,32 +507,23 @@ __global__ void __launch_bounds__(kBlock, 3) k_render_bwd(const RenderArgs A)
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) wl = max(wl, __shfl_xor_sync(0xFFFFFFFFu, wl, o));
 
-        for (int ch = ((wl - 1) >> 5) << 5; ch >= 0 && wl > 0; ch -= 32) {
-            const int jl = ch + lane;   // list position of this lane's entry
-            bool rel = false;
+        // stage queue entries [0, cnt) (in decreasing list order), replay and differentiate them
+        // back to front, then flush each staged primitive's sums (lane b flushes slot b)
+        auto adjoint = [&](int cnt) {
             Prim pr;
             pr.i = -1;
-            if (jl < wl) {
-                const uint32_t p = A.sorted_vals[rg.x + jl];
-                const PairRec rec = A.recs[p];
-                const uint32_t rect = local_rect<TH, TW>(rec, ti);
-                rel = rect_meets_block(rect, bp.br, bp.bc);
-                if (rel) {
-                    stage(A, ti, p, rec, rect, slots[lane], pr);
+            if (lane < cnt) {
+                stage(A, ti, q.p[lane], (q.pos[lane] >> 31) != 0, q.rect[lane], slots[lane], pr);
 #pragma unroll
-                    for (int q = 0; q < kAcc; ++q) acc[lane][q] = 0.0f;
-                }
+                for (int j = 0; j < kAcc; ++j) acc[lane][j] = 0.0f;
             }
-            uint32_t m = __ballot_sync(0xFFFFFFFFu, rel);
             __syncwarp();
-            while (m) {
-                const int b = 31 - __clz(m);
-                m &= ~(1u << b);
-                const int k = ch + b;
+            for (int b = 0; b < cnt; ++b) {
+                const int k = static_cast<int>(q.pos[b] & 0x7FFFFFFFu);
                 const Staged &s = slots[b];
                 float g[16];
 #pragma unroll
-                for (int q = 0; q < 16; ++q) g[q] = 0.0f;
+                for (int c = 0; c < 16; ++c) g[c] = 0.0f;
                 bool contrib = false;
                 if (k < nl && in_rect(__float_as_uint(s.b.w), bp.lr, bp.lc)) {
                     ++evals;
@@ -543,23 +582,23 @@ __global__ void __launch_bounds__(kBlock, 3) k_render_bwd(const RenderArgs A)
                 }
                 const uint32_t cm = __ballot_sync(0xFFFFFFFFu, contrib);
                 if (cm == 0u) continue;
-                if (__popc(cm) <= kDirectLanes) {
+                if ((cm & (cm - 1u)) == 0u) {   // a single contributing lane: a plain add
                     if (contrib) {
 #pragma unroll
-                        for (int q = 0; q < 13; ++q) atomicAdd(&acc[b][q], g[q]);
+                        for (int c = 0; c < 13; ++c) acc[b][c] += g[c];
                     }
                 } else {
                     const float tot = warp_reduce16(g, lane);
-                    const int q = reduced_index(lane);
-                    if (lane < 16 && q < 13) acc[b][q] += tot;
+                    const int c = reduced_index(lane);
+                    if (lane < 16 && c < 13) acc[b][c] += tot;
                 }
             }
             __syncwarp();
-            if (rel) {
+            if (lane < cnt) {
                 const float *a = acc[lane];
                 bool any = false;
 #pragma unroll
-                for (int q = 0; q < 13; ++q) any |= a[q] != 0.0f;
+                for (int c = 0; c < 13; ++c) any |= a[c] != 0.0f;
                 if (any) {
                     const float *M = ti.M_hi;
                     const float *R = ti.R;
@@ -584,7 +623,35 @@ __global__ void __launch_bounds__(kBlock, 3) k_render_bwd(const RenderArgs A)
                 }
             }
             __syncwarp();
+        };
+
+        int qn = 0;
+        for (int ch = ((wl - 1) >> 5) << 5; ch >= 0 && wl > 0; ch -= 32) {
+            const int jl = ch + lane;   // list position of this lane's entry
+            bool rel = false, flip = false;
+            uint32_t p = 0, rect = 0;
+            if (jl < wl) rel = read_entry<TH, TW>(A, ti, rg.x + jl, bp, p, rect, flip);
+            const uint32_t m = __ballot_sync(0xFFFFFFFFu, rel);
+            if (rel) {   // queue in decreasing list position: higher lanes first
+                const int pos = qn + __popc(m & gt_mask);
+                q.p[pos] = p;
+                q.rect[pos] = rect;
+                q.pos[pos] = static_cast<uint32_t>(jl) | (flip ? 0x80000000u : 0u);
+            }
+            qn += __popc(m);
+            __syncwarp();
+            if (qn >= 32) {
+                adjoint(32);
+                if (lane < qn - 32) {
+                    q.p[lane] = q.p[32 + lane];
+                    q.rect[lane] = q.rect[32 + lane];
+                    q.pos[lane] = q.pos[32 + lane];
+                }
+                qn -= 32;
+                __syncwarp();
+            }
         }
+        if (qn > 0) adjoint(qn);
     }
     warp_count(evals, A.evals);
 }
