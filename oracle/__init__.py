@@ -61,7 +61,9 @@ def _load():
             lib.or_contract_expf.argtypes = [_F]
             lib.or_contract_expf.restype = _F
             lib.or_project_contract.argtypes = [_I64, _P, _P, _P, _P, _I, _I, _F, _F, _I, _I,
-                                                _F, _I, _P, _P, _P, _P, _P, _P]
+                                                _F, _F, _I, _P, _P, _P, _P, _P, _P]
+            lib.or_contract_logf.argtypes = [_F]
+            lib.or_contract_logf.restype = _F
             lib.or_bin.argtypes = [_I64, _P, _P, _P, _I, _I, _I, _I, _I64, _P, _P, _I64]
             lib.or_bin.restype = _I64
             lib.or_tile_ranges.argtypes = [_I64, _P, _I64, _I64, _P, _P]
@@ -113,8 +115,12 @@ def contract_expf(x) -> float:
     return float(_load().or_contract_expf(float(np.float32(x))))
 
 
+def contract_logf(x) -> float:
+    return float(_load().or_contract_logf(float(np.float32(x))))
+
+
 def project_contract(pos_logit, quat, log_scale, T_ws, rows, cols, elev_min, elev_max,
-                     tile_h=16, tile_w=16, sigma_cut=3.0, flip_normals=1):
+                     tile_h=16, tile_w=16, sigma_cut=3.0, flip_normals=1, alpha_min=1.0 / 255.0):
     """Binary32 contract for one view: kappa, flip (+1/-1), pixel rect (r0, r1, c0, nc),
     tile rect (tr0, tr1, tc0, ntc), tile count, valid flag."""
     pl = _c(pos_logit, np.float32)
@@ -131,7 +137,8 @@ def project_contract(pos_logit, quat, log_scale, T_ws, rows, cols, elev_min, ele
     _load().or_project_contract(n, _ptr(pl), _ptr(q), _ptr(ls), _ptr(T),
                                 rows, cols, float(np.float32(elev_min)),
                                 float(np.float32(elev_max)), tile_h, tile_w,
-                                float(np.float32(sigma_cut)), int(flip_normals),
+                                float(np.float32(sigma_cut)), float(np.float32(alpha_min)),
+                                int(flip_normals),
                                 _ptr(kappa), _ptr(flip), _ptr(pix), _ptr(til), _ptr(cnt),
                                 _ptr(valid))
     return dict(kappa=kappa, flip=flip, pix_rect=pix, tile_rect=til, count=cnt, valid=valid)
@@ -302,7 +309,7 @@ def full_view(pos_logit, quat, log_scale, T_ws, rows, cols, elev_min, elev_max, 
               n_threads=0):
     """Convenience: contract + binning + FP64 render of one view from FP32 inputs."""
     proj = project_contract(pos_logit, quat, log_scale, T_ws, rows, cols, elev_min, elev_max,
-                            tile_h, tile_w, cfg[3], flip_normals)
+                            tile_h, tile_w, cfg[3], flip_normals, cfg[0])
     params = split_params(pos_logit, quat, log_scale)
     emin, emax = float(np.float32(elev_min)), float(np.float32(elev_max))
     if mode == "culled":

@@ -58,7 +58,7 @@
 
 #define OR_PI 3.14159265358979323846
 
-int or_version(void) { return 4; }
+int or_version(void) { return 5; }
 
 /* ------------------------------------------------------------------------- */
 /* 1. pose                                                                   */
@@ -182,50 +182,97 @@ static int contract_vectors(const float *pl, const float *q, const float *ls,
     return 1;
 }
 
-/* Contract step C4: conservative spherical bounding box of the 3-sigma
- * parallelogram F = {b_c + a b_alpha + b b_beta : |a|,|b| <= sigma} (Sec. 3.2.3;
- * Supp. B relaxes the tight quartic box to the projected vertices, which misses
- * the elevation bulge of an edge: here every edge's interior elevation extremum
- * is added, and the poles and the sensor-inside case are handled).
- *
- * Azimuth: if the xy-projection of F contains the z axis (with a small
- * tolerance) every column is covered; otherwise the azimuths of F span less
- * than pi and their extremes are at the corners, measured relative to the
- * centre direction so that the +-pi seam needs no case.
- * Elevation: extremes over the boundary (corners, plus the one interior
- * extremum an edge can have, where d/dlambda of z/|xy| vanishes on
- * P + lambda (Q - P)), widened to +-pi/2 when the z axis pierces F above or
- * below the sensor.
- * Out: pixel rows [r0, r1], cyclic pixel columns [c0, c0 + nc) mod W, tile
- * rows [tr0, tr1], cyclic tile columns [tc0, tc0 + ntc) mod TC.  Returns the
- * number of tiles (0 when no pixel ray can reach F). */
-static int contract_bbox(f3 ba, f3 bb, f3 bc, float sigma, int H, int W,
-                         float emin, float emax, int th, int tw,
-                         int32_t *pix, int32_t *til)
+/* ln for the contract, x >= 1: x = 2^e m with m folded into [1/sqrt2, sqrt2), then
+ * ln m = 2 atanh z, z = (m - 1)/(m + 1), |z| <= 0.172, from the series 2(z + z^3/3 + ... + z^9/9)
+ * (next term < 3e-10). */
+float or_contract_logf(float x)
+{
+    uint32_t u;
+    memcpy(&u, &x, 4);
+    int e = (int)((u >> 23) & 0xFF) - 127;
+    uint32_t mu = (u & 0x7FFFFFu) | 0x3F800000u;
+    float m;
+    memcpy(&m, &mu, 4);
+    if (m > 1.41421354f) { m = m * 0.5f; e = e + 1; }
+    float z = (m - 1.0f) / (m + 1.0f);
+    float z2 = z * z;
+    float p = 0.111111111f;          /* 1/9 */
+    p = fmaf(p, z2, 0.142857143f);   /* 1/7 */
+    p = fmaf(p, z2, 0.2f);           /* 1/5 */
+    p = fmaf(p, z2, 0.333333333f);   /* 1/3 */
+    p = fmaf(p, z2, 1.0f);
+    return fmaf((float)e, 0.693147182f, 2.0f * z * p);
+}
+
+/* Contract step C4: conservative spherical bounding box of the splat-space region where the
+ * primitive can contribute: the 3-sigma box |s|_inf <= sigma (Sec. 3.2.3) intersected with the
+ * disk where o G(s) >= alpha_min, i.e. |s| <= r_o = sqrt(2 ln(o / alpha_min)) (the alpha_min
+ * cutoff of the blending), bounded by the polygon |s|_inf <= a = min(sigma, r_o) and
+ * |s_a| + |s_b| <= sqrt2 r_o (an octagon when it cuts the square's corners), with a 0.1 % + 0.002
+ * margin on r_o.  The polygon is mapped to the sensor frame, P = b_c + s_a b_a + s_b b_b.
+ * Supp. B relaxes the tight quartic box to the projected vertices, which misses the elevation
+ * bulge of an edge: here every edge's interior elevation extremum is added, and the poles and
+ * the sensor-inside case are handled.
+ * Azimuth: if the xy-projection of the polygon contains the z axis (with a small tolerance)
+ * every column is covered; otherwise the azimuths span less than pi and their extremes are at the
+ * vertices, measured relative to the centre direction so that the +-pi seam needs no case.
+ * Elevation: extremes over the boundary (vertices, plus the one interior extremum an edge can
+ * have, where d/dlambda of z/|xy| vanishes on P + lambda (Q - P)), widened to +-pi/2 when the
+ * z axis pierces the polygon above or below the sensor.
+ * Out: pixel rows [r0, r1], cyclic pixel columns [c0, c0 + nc) mod W, tile rows [tr0, tr1],
+ * cyclic tile columns [tc0, tc0 + ntc) mod TC.  Returns the number of tiles (0 when no pixel ray
+ * can reach the region). */
+static int contract_bbox(f3 ba, f3 bb, f3 bc, float o, float alpha_min, float sigma, int H,
+                         int W, float emin, float emax, int th, int tw, int32_t *pix,
+                         int32_t *til)
 {
     const float eps = 0.01f; /* pixel-unit margin */
-    f3 A = { sigma * ba.x, sigma * ba.y, sigma * ba.z };
-    f3 B = { sigma * bb.x, sigma * bb.y, sigma * bb.z };
+    float x = o / alpha_min;
+    if (x < 0.999f) return 0;
+    if (x < 1.0f) x = 1.0f;
+    float ro = sqrtf(2.0f * or_contract_logf(x)) * 1.001f + 0.002f;
+    float a = ro < sigma ? ro : sigma;
+    float k = (1.41421356f * ro) / a;   /* diamond |u| + |v| <= k in units of a */
+    f3 A = { a * ba.x, a * ba.y, a * ba.z };
+    f3 B = { a * bb.x, a * bb.y, a * bb.z };
     f3 C = bc;
-    f3 P[4];
-    P[0].x = (C.x - A.x) - B.x; P[0].y = (C.y - A.y) - B.y; P[0].z = (C.z - A.z) - B.z;
-    P[1].x = (C.x + A.x) - B.x; P[1].y = (C.y + A.y) - B.y; P[1].z = (C.z + A.z) - B.z;
-    P[2].x = (C.x + A.x) + B.x; P[2].y = (C.y + A.y) + B.y; P[2].z = (C.z + A.z) + B.z;
-    P[3].x = (C.x - A.x) + B.x; P[3].y = (C.y - A.y) + B.y; P[3].z = (C.z - A.z) + B.z;
+    float uv[16];
+    int nv;
+    if (k < 2.0f) {
+        float c = k - 1.0f;
+        float t[16] = { 1.0f, -c, 1.0f, c, c, 1.0f, -c, 1.0f,
+                        -1.0f, c, -1.0f, -c, -c, -1.0f, c, -1.0f };
+        memcpy(uv, t, sizeof t);
+        nv = 8;
+    } else {
+        float t[8] = { -1.0f, -1.0f, 1.0f, -1.0f, 1.0f, 1.0f, -1.0f, 1.0f };
+        memcpy(uv, t, sizeof t);
+        nv = 4;
+    }
+    f3 P[8];
+    for (int i = 0; i < nv; ++i) {
+        float u = uv[2 * i], v = uv[2 * i + 1];
+        P[i].x = (C.x + u * A.x) + v * B.x;
+        P[i].y = (C.y + u * A.y) + v * B.y;
+        P[i].z = (C.z + u * A.z) + v * B.z;
+    }
 
-    float o = A.x * B.y - A.y * B.x;
+    /* does the z axis cross the xy-shadow of the polygon?  c + u A + v B = 0 with |u|, |v| <= 1
+     * and |u| + |v| <= k */
+    float det = A.x * B.y - A.y * B.x;
     float ca = C.x * B.y - C.y * B.x;
     float cb = A.x * C.y - A.y * C.x;
     float la = fabsf(A.x) + fabsf(A.y), lb = fabsf(B.x) + fabsf(B.y);
     float lc = fabsf(C.x) + fabsf(C.y);
     float tol = 1e-5f * ((la + lb) * ((lc + la) + lb));
-    float ao = fabsf(o);
-    int inside = (fabsf(ca) <= ao + tol) && (fabsf(cb) <= ao + tol);
+    float ad = fabsf(det);
+    int inside = (fabsf(ca) <= ad + tol) && (fabsf(cb) <= ad + tol) &&
+                 (fabsf(ca) + fabsf(cb) <= k * ad + 2.0f * tol);
     int pole_n = 0, pole_s = 0;
     if (inside) {
-        if (ao > tol) {
-            float a = -ca / o, b = -cb / o;
-            float zh = (C.z + a * A.z) + b * B.z;
+        if (ad > tol) {
+            float u = -ca / det, v = -cb / det;
+            float zh = (C.z + u * A.z) + v * B.z;
             float tz = 1e-5f * ((fabsf(C.z) + fabsf(A.z)) + fabsf(B.z));
             pole_n = zh > -tz;
             pole_s = zh < tz;
@@ -235,8 +282,8 @@ static int contract_bbox(f3 ba, f3 bb, f3 bc, float sigma, int H, int W,
     }
 
     float th_lo = INFINITY, th_hi = -INFINITY;
-    for (int i = 0; i < 4; ++i) {
-        f3 p = P[i], q = P[(i + 1) & 3];
+    for (int i = 0; i < nv; ++i) {
+        f3 p = P[i], q = P[(i + 1) % nv];
         float rxy = sqrtf(p.x * p.x + p.y * p.y);
         float e = or_contract_atan2f(p.z, rxy);
         th_lo = fminf(th_lo, e); th_hi = fmaxf(th_hi, e);
@@ -272,7 +319,7 @@ static int contract_bbox(f3 ba, f3 bb, f3 bc, float sigma, int H, int W,
     } else {
         float gc = or_contract_atan2f(C.y, C.x);
         float dmin = INFINITY, dmax = -INFINITY;
-        for (int i = 0; i < 4; ++i) {
+        for (int i = 0; i < nv; ++i) {
             float cr = C.x * P[i].y - C.y * P[i].x;
             float dt = C.x * P[i].x + C.y * P[i].y;
             float dl = or_contract_atan2f(cr, dt);
@@ -305,7 +352,8 @@ static int contract_bbox(f3 ba, f3 bb, f3 bc, float sigma, int H, int W,
     return (tr1 - tr0 + 1) * ntc;
 }
 
-/* The binary32 contract for n primitives in one view.
+/* The binary32 contract for n primitives in one view (o = 1/(1 + exp(-logit)) in the
+ * contract's arithmetic feeds the contributing region of the bounding box).
  * kappa: f32 centre range |b_c| (the range the per-tile lists are sorted by,
  * Sec. 3.2.1); flip: -1 when the sensor-frame normal R_cw t_n points away from
  * the sensor ((n . b_c) > 0) and flip_normals is set, else +1; pix_rect, tile_rect,
@@ -314,8 +362,8 @@ static int contract_bbox(f3 ba, f3 bb, f3 bc, float sigma, int H, int W,
 void or_project_contract(int64_t n, const float *pos_logit, const float *quat,
                          const float *log_scale, const double *T_ws,
                          int rows, int cols, float elev_min, float elev_max,
-                         int tile_h, int tile_w, float sigma_cut, int flip_normals,
-                         float *kappa, int8_t *flip, int32_t *pix_rect,
+                         int tile_h, int tile_w, float sigma_cut, float alpha_min,
+                         int flip_normals, float *kappa, int8_t *flip, int32_t *pix_rect,
                          int32_t *tile_rect, int32_t *count, uint8_t *valid)
 {
     double Rd[9], td[3];
@@ -333,8 +381,9 @@ void or_project_contract(int64_t n, const float *pos_logit, const float *quat,
         float dot = (nr.x * bc.x + nr.y * bc.y) + nr.z * bc.z;
         flip[i] = (flip_normals && dot > 0.0f) ? (int8_t)-1 : (int8_t)1;
         kappa[i] = sqrtf((bc.x * bc.x + bc.y * bc.y) + bc.z * bc.z);
-        count[i] = contract_bbox(ba, bb, bc, sigma_cut, rows, cols, elev_min, elev_max,
-                                 tile_h, tile_w, pix_rect + 4 * i, tile_rect + 4 * i);
+        float oc = 1.0f / (1.0f + or_contract_expf(-pos_logit[4 * i + 3]));
+        count[i] = contract_bbox(ba, bb, bc, oc, alpha_min, sigma_cut, rows, cols, elev_min,
+                                 elev_max, tile_h, tile_w, pix_rect + 4 * i, tile_rect + 4 * i);
     }
 }
 

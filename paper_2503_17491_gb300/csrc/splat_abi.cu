@@ -168,7 +168,8 @@ int render_core(splat_ctx *ctx, const splat_gaussians *g, float *depth, float *n
     CK(splat::launch_project(reinterpret_cast<const float4 *>(g->pos_logit),
                              reinterpret_cast<const float4 *>(g->quat_wxyz),
                              reinterpret_cast<const float2 *>(g->log_scale), n, ctx->d_views,
-                             ctx->n_views, ctx->cfg.sigma_cut, th, tw, ctx->cfg.flip_normals,
+                             ctx->n_views, ctx->cfg.sigma_cut, ctx->cfg.alpha_min, th, tw,
+                             ctx->cfg.flip_normals,
                              ctx->d_recs, ctx->d_dkeys, ctx->d_dvals, cnt + 1, st));
     uint32_t *dk, *dv;
     CK(splat::radix_sort_pairs(ctx->d_dkeys, ctx->d_dvals, ctx->d_dkeys2, ctx->d_dvals2, nullptr,

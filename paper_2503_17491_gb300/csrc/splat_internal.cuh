@@ -206,9 +206,10 @@ __device__ __forceinline__ void chain_params(const float4 pl, const float4 q, co
 struct Workspace;   // host-side bookkeeping, defined in splat_abi.cu
 
 cudaError_t launch_project(const float4 *pos_logit, const float4 *quat, const float2 *log_scale,
-                           int64_t n, const ViewDesc *views, int n_views, float sigma, int tile_h,
-                           int tile_w, int flip_normals, PairRec *recs, uint32_t *dkeys,
-                           uint32_t *dvals, uint32_t *status, cudaStream_t st);
+                           int64_t n, const ViewDesc *views, int n_views, float sigma,
+                           float alpha_min, int tile_h, int tile_w, int flip_normals,
+                           PairRec *recs, uint32_t *dkeys, uint32_t *dvals, uint32_t *status,
+                           cudaStream_t st);
 
 // stable LSD radix sort of (uint32 key, uint32 value) pairs on key bits [0, bits);
 // the count is read on the device from *d_count (clamped to max_n); result lands in

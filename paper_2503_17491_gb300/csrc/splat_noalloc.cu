@@ -269,7 +269,8 @@ extern "C" SPLAT_API int splat_render_noalloc(const splat_gaussians *g,
     NA_CK(splat::launch_project(reinterpret_cast<const float4 *>(g->pos_logit),
                                 reinterpret_cast<const float4 *>(g->quat_wxyz),
                                 reinterpret_cast<const float2 *>(g->log_scale), n, view, 1,
-                                cfg.sigma_cut, th, tw, cfg.flip_normals, recs, dkeys, dvals,
+                                cfg.sigma_cut, cfg.alpha_min, th, tw, cfg.flip_normals, recs, dkeys,
+                                dvals,
                                 cnt + 1, st));
     uint32_t *dk, *dv;
     NA_CK(splat::radix_sort_pairs(dkeys, dvals, dkeys2, dvals2, nullptr, n, 32, hist, &dk, &dv, st));

@@ -1,14 +1,14 @@
 // K1: per-primitive projection for every registered view -- the range key, the sign that turns
-// the normal towards the sensor, and the conservative spherical bounding box of the 3-sigma
-// parallelogram with its tile rectangle (Sec. 3.2.1 tiles and range sort; Sec. 3.2.3 bounding
+// the normal towards the sensor, and the conservative spherical bounding box of the region of the
+// 3-sigma box where the primitive can reach alpha_min, with its tile rectangle (Sec. 3.2.1 tiles and range sort; Sec. 3.2.3 bounding
 // box computation; Supp. B).
 //
 // Everything in this file takes integer decisions (which tiles, which order, which sign), so it
 // follows a fixed binary32 contract: every value is produced by the same sequence of correctly
 // rounded IEEE operations on every machine.  The file is compiled with -fmad=false so that no
 // a*b+c is fused; fused multiply-adds appear only where written as fmaf.  The arctangent and
-// exponential used by the contract are evaluated from their series (see contract_atan2 and
-// contract_exp), never through a math library.
+// exponential and logarithm used by the contract are evaluated from their series (see
+// contract_atan2, contract_exp, contract_log), never through a math library.
 //
 // One thread per primitive reads its 40 bytes once (coalesced float4/float2 loads) and loops
 // over the views; each (view, primitive) record is 16 bytes.  The range-sort keys and pair ids
@@ -82,6 +82,27 @@ __device__ float contract_exp(float x)
     return p * __uint_as_float(static_cast<uint32_t>(ki + 127) << 23);
 }
 
+// ln for the contract, x >= 1: x = 2^e m with m folded into [1/sqrt2, sqrt2), then
+// ln m = 2 atanh z, z = (m - 1)/(m + 1), from the series 2(z + z^3/3 + ... + z^9/9).
+__device__ float contract_log(float x)
+{
+    const uint32_t u = __float_as_uint(x);
+    int e = static_cast<int>((u >> 23) & 0xFFu) - 127;
+    float m = __uint_as_float((u & 0x7FFFFFu) | 0x3F800000u);
+    if (m > 1.41421354f) {
+        m = m * 0.5f;
+        e = e + 1;
+    }
+    const float z = (m - 1.0f) / (m + 1.0f);
+    const float z2 = z * z;
+    float p = 0.111111111f;
+    p = fmaf(p, z2, 0.142857143f);
+    p = fmaf(p, z2, 0.2f);
+    p = fmaf(p, z2, 0.333333333f);
+    p = fmaf(p, z2, 1.0f);
+    return fmaf(static_cast<float>(e), 0.693147182f, 2.0f * z * p);
+}
+
 struct v3 {
     float x, y, z;
 };
@@ -93,24 +114,57 @@ __device__ __forceinline__ v3 rot(const float *R, v3 v)
               (R[6] * v.x + R[7] * v.y) + R[8] * v.z};
 }
 
-// Spherical bounding box of F = {b_c + a A + b B : |a|, |b| <= 1} with A = sigma b_alpha,
-// B = sigma b_beta.  Azimuth: every column when the z axis pierces the xy-shadow of F, else the
-// corner azimuths relative to the centre direction.  Elevation: corners, each edge's interior
-// extremum (where z / |xy| is stationary along the edge), and the pole the z axis reaches.
-// Returns the tile count and fills the record's pixel rectangle.
-__device__ uint32_t contract_bbox(v3 ba, v3 bb, v3 bc, float sigma, const ViewDesc &vd,
-                                  int tile_h, int tile_w, PairRec &rec)
+// Spherical bounding box of the splat-space region where the primitive can contribute: the
+// 3-sigma box |s|_inf <= sigma intersected with the disk where o G(s) >= alpha_min, i.e.
+// |s| <= r_o = sqrt(2 ln(o / alpha_min)), bounded by |s|_inf <= a = min(sigma, r_o) and the
+// diamond |s_a| + |s_b| <= sqrt2 r_o (an octagon when it cuts the corners), r_o widened by
+// 0.1 % + 0.002.  The polygon maps to P = b_c + s_a b_alpha + s_b b_beta.  Azimuth: every column
+// when the z axis pierces the polygon's xy-shadow, else the vertex azimuths relative to the
+// centre direction.  Elevation: vertices, each edge's interior extremum (where z / |xy| is
+// stationary along the edge), and the pole the z axis reaches.  Returns the tile count and
+// fills the record's pixel rectangle.
+__device__ uint32_t contract_bbox(v3 ba, v3 bb, v3 bc, float o, float alpha_min, float sigma,
+                                  const ViewDesc &vd, int tile_h, int tile_w, PairRec &rec)
 {
-    const v3 A{sigma * ba.x, sigma * ba.y, sigma * ba.z};
-    const v3 B{sigma * bb.x, sigma * bb.y, sigma * bb.z};
+    float x = o / alpha_min;
+    if (x < 0.999f) return 0u;
+    if (x < 1.0f) x = 1.0f;
+    const float ro = sqrtf(2.0f * contract_log(x)) * 1.001f + 0.002f;
+    const float a = ro < sigma ? ro : sigma;
+    const float k = (1.41421356f * ro) / a;
+    const v3 A{a * ba.x, a * ba.y, a * ba.z};
+    const v3 B{a * bb.x, a * bb.y, a * bb.z};
     const v3 C = bc;
-    v3 P[4];
-    P[0] = v3{(C.x - A.x) - B.x, (C.y - A.y) - B.y, (C.z - A.z) - B.z};
-    P[1] = v3{(C.x + A.x) - B.x, (C.y + A.y) - B.y, (C.z + A.z) - B.z};
-    P[2] = v3{(C.x + A.x) + B.x, (C.y + A.y) + B.y, (C.z + A.z) + B.z};
-    P[3] = v3{(C.x - A.x) + B.x, (C.y - A.y) + B.y, (C.z - A.z) + B.z};
+    float u[8], w[8];
+    int nv;
+    if (k < 2.0f) {
+        const float c = k - 1.0f;
+        u[0] = 1.0f;  w[0] = -c;
+        u[1] = 1.0f;  w[1] = c;
+        u[2] = c;     w[2] = 1.0f;
+        u[3] = -c;    w[3] = 1.0f;
+        u[4] = -1.0f; w[4] = c;
+        u[5] = -1.0f; w[5] = -c;
+        u[6] = -c;    w[6] = -1.0f;
+        u[7] = c;     w[7] = -1.0f;
+        nv = 8;
+    } else {
+        u[0] = -1.0f; w[0] = -1.0f;
+        u[1] = 1.0f;  w[1] = -1.0f;
+        u[2] = 1.0f;  w[2] = 1.0f;
+        u[3] = -1.0f; w[3] = 1.0f;
+        nv = 4;
+    }
+    v3 P[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        if (i < nv)
+            P[i] = v3{(C.x + u[i] * A.x) + w[i] * B.x, (C.y + u[i] * A.y) + w[i] * B.y,
+                      (C.z + u[i] * A.z) + w[i] * B.z};
+    }
 
-    // does the z axis cross the xy-shadow of F?  c + a A + b B = 0 with |a|, |b| <= 1
+    // does the z axis cross the polygon's xy-shadow?  c + u A + w B = 0 with |u|, |w| <= 1 and
+    // |u| + |w| <= k
     const float det = A.x * B.y - A.y * B.x;
     const float cxb = C.x * B.y - C.y * B.x;
     const float axc = A.x * C.y - A.y * C.x;
@@ -118,12 +172,13 @@ __device__ uint32_t contract_bbox(v3 ba, v3 bb, v3 bc, float sigma, const ViewDe
     const float lc = fabsf(C.x) + fabsf(C.y);
     const float tol = 1e-5f * ((la + lb) * ((lc + la) + lb));
     const float adet = fabsf(det);
-    const bool axis_in = (fabsf(cxb) <= adet + tol) && (fabsf(axc) <= adet + tol);
+    const bool axis_in = (fabsf(cxb) <= adet + tol) && (fabsf(axc) <= adet + tol) &&
+                         (fabsf(cxb) + fabsf(axc) <= k * adet + 2.0f * tol);
     bool north = false, south = false;
     if (axis_in) {
         if (adet > tol) {
-            const float a = -cxb / det, b = -axc / det;
-            const float zh = (C.z + a * A.z) + b * B.z;
+            const float uu = -cxb / det, ww = -axc / det;
+            const float zh = (C.z + uu * A.z) + ww * B.z;
             const float tz = 1e-5f * ((fabsf(C.z) + fabsf(A.z)) + fabsf(B.z));
             north = zh > -tz;
             south = zh < tz;
@@ -133,9 +188,8 @@ __device__ uint32_t contract_bbox(v3 ba, v3 bb, v3 bc, float sigma, const ViewDe
     }
 
     float el_lo = INFINITY, el_hi = -INFINITY;
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-        const v3 p = P[i], q = P[(i + 1) & 3];
+    for (int i = 0; i < nv; ++i) {
+        const v3 p = P[i], q = P[(i + 1) % nv];
         const float e = contract_atan2(p.z, sqrtf(p.x * p.x + p.y * p.y));
         el_lo = fminf(el_lo, e);
         el_hi = fmaxf(el_hi, e);
@@ -174,8 +228,7 @@ __device__ uint32_t contract_bbox(v3 ba, v3 bb, v3 bc, float sigma, const ViewDe
     } else {
         const float gc = contract_atan2(C.y, C.x);
         float dmin = INFINITY, dmax = -INFINITY;
-#pragma unroll
-        for (int i = 0; i < 4; ++i) {
+        for (int i = 0; i < nv; ++i) {
             const float cr = C.x * P[i].y - C.y * P[i].x;
             const float dt = C.x * P[i].x + C.y * P[i].y;
             const float dl = contract_atan2(cr, dt);
@@ -209,7 +262,8 @@ __device__ uint32_t contract_bbox(v3 ba, v3 bb, v3 bc, float sigma, const ViewDe
 __global__ void __launch_bounds__(256) k_project(
     const float4 *__restrict__ pos_logit, const float4 *__restrict__ quat,
     const float2 *__restrict__ log_scale, int64_t n, const ViewDesc *__restrict__ views,
-    int n_views, float sigma, int tile_h, int tile_w, int flip_normals, PairRec *__restrict__ recs,
+    int n_views, float sigma, float alpha_min, int tile_h, int tile_w, int flip_normals,
+    PairRec *__restrict__ recs,
     uint32_t *__restrict__ dkeys, uint32_t *__restrict__ dvals, uint32_t *__restrict__ status)
 {
     const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
@@ -226,7 +280,7 @@ __global__ void __launch_bounds__(256) k_project(
     const float qq = ((w * w + x * x) + y * y) + z * z;
     ok = ok && qq > 0.0f && isfinite(qq);
     v3 ta{}, tb{}, tn{};
-    float sa = 0.0f, sb = 0.0f;
+    float sa = 0.0f, sb = 0.0f, oc = 0.0f;
     if (ok) {
         const float r = sqrtf(qq);
         w = w / r;
@@ -239,6 +293,7 @@ __global__ void __launch_bounds__(256) k_project(
         tn = v3{2.0f * (x * z + w * y), 2.0f * (y * z - w * x), 1.0f - 2.0f * (x * x + y * y)};
         sa = contract_exp(ls.x);
         sb = contract_exp(ls.y);
+        oc = 1.0f / (1.0f + contract_exp(-pl.w));
     } else {
         atomicOr(status, SPLAT_STATUS_NONFINITE);
     }
@@ -262,7 +317,7 @@ __global__ void __launch_bounds__(256) k_project(
             if (flip_normals && dot > 0.0f) rec.cf |= kPairFlip;
             rec.kappa = sqrtf((bc.x * bc.x + bc.y * bc.y) + bc.z * bc.z);
             // C4: bounding box
-            rec.cf |= contract_bbox(ba, bb, bc, sigma, vd, tile_h, tile_w, rec);
+            rec.cf |= contract_bbox(ba, bb, bc, oc, alpha_min, sigma, vd, tile_h, tile_w, rec);
         }
         recs[p] = rec;
         dkeys[p] = (rec.cf & kCountMask) ? __float_as_uint(rec.kappa) : 0xFFFFFFFFu;
@@ -273,14 +328,16 @@ __global__ void __launch_bounds__(256) k_project(
 }  // namespace
 
 cudaError_t launch_project(const float4 *pos_logit, const float4 *quat, const float2 *log_scale,
-                           int64_t n, const ViewDesc *views, int n_views, float sigma, int tile_h,
-                           int tile_w, int flip_normals, PairRec *recs, uint32_t *dkeys,
-                           uint32_t *dvals, uint32_t *status, cudaStream_t st)
+                           int64_t n, const ViewDesc *views, int n_views, float sigma,
+                           float alpha_min, int tile_h, int tile_w, int flip_normals,
+                           PairRec *recs, uint32_t *dkeys, uint32_t *dvals, uint32_t *status,
+                           cudaStream_t st)
 {
     if (n <= 0) return cudaSuccess;
     const unsigned grid = static_cast<unsigned>((n + 255) / 256);
-    k_project<<<grid, 256, 0, st>>>(pos_logit, quat, log_scale, n, views, n_views, sigma, tile_h,
-                                    tile_w, flip_normals, recs, dkeys, dvals, status);
+    k_project<<<grid, 256, 0, st>>>(pos_logit, quat, log_scale, n, views, n_views, sigma,
+                                    alpha_min, tile_h, tile_w, flip_normals, recs, dkeys, dvals,
+                                    status);
     return cudaGetLastError();
 }
 

@@ -197,3 +197,23 @@ def test_invalid_arguments_are_rejected():
     T[0, 3] = math.inf
     with pytest.raises(api._lib.SplatError):
         ctx.set_views([scenes.View(T, 16, 64, -0.1, 0.1)])
+
+
+def test_workload4_map_size_batched_sampled():
+    """The long mapping run's largest state: a 3,000,000-primitive map and its 8 most recent
+    128x1024 scans (mid-trajectory) in one batched call; sampled pixels of three scans are
+    composited by the oracle."""
+    s = scenes.workload(4, n=3_000_000)
+    views = s.views[100:108]
+    ctx, d, n, a = _render(s, views)
+    assert ctx.status() == 0
+    rng = np.random.default_rng(4)
+    for k in (0, 3, 7):
+        v = views[k]
+        r = rng.integers(0, v.rows, 2048)
+        c = rng.integers(0, v.cols, 2048)
+        rr = np.concatenate([r, np.full(v.cols, v.rows // 2)])
+        cc = np.concatenate([c, np.arange(v.cols)])
+        ref, *_ = oracle_view(s, v, pixels=np.stack([rr, cc], 1))
+        idx = ctx.offsets[k] + rr * v.cols + cc
+        compare_images(d[idx], n[:, idx], a[idx], ref, f"workload4 scan {k}")

@@ -43,6 +43,24 @@ def test_contract_exp_bound(oracle_mod):
     assert oracle_mod.contract_expf(1.0) == pytest.approx(math.e, rel=2e-7)
 
 
+def test_contract_log_bound(oracle_mod):
+    xs = np.exp(np.linspace(0.0, np.log(1e6), 20001)).astype(np.float32)
+    # within a few float ulps of ln x (the series truncation is ~1e-9 at |z| <= 0.172)
+    worst = max(abs(oracle_mod.contract_logf(x) - math.log(float(x))) / max(1.0, math.log(float(x)))
+                for x in xs[::7])
+    assert worst < 1.2e-7
+    assert oracle_mod.contract_logf(1.0) == 0.0
+    assert oracle_mod.contract_logf(2.0) == pytest.approx(math.log(2.0), abs=3e-7)
+
+
+def test_low_opacity_primitive_reaches_nothing(oracle_mod):
+    """A primitive whose opacity is below alpha_min can never contribute: no tiles."""
+    pl, q, ls = _single((5.0, 0.0, 0.0), (0.5, 0.5, 0.5, 0.5), (0.3, 0.3), o=0.003)
+    v = scenes.View(np.eye(4), 32, 512, scenes.deg(-15), scenes.deg(15))
+    proj = oracle_mod.project_contract(pl, q, ls, v.T_ws, v.rows, v.cols, v.elev_min, v.elev_max)
+    assert proj["count"][0] == 0
+
+
 def test_pose_inverse(oracle_mod):
     T = scenes.random_pose(np.random.default_rng(1), 5.0, 40.0)
     R, t = oracle_mod.pose_inverse(T)
