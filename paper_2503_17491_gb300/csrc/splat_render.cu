@@ -3,15 +3,20 @@
 // parameters.
 //
 // Work decomposition.  A work item is one 4 x 8 pixel block of one tile (a tile is
-// tile_h x tile_w = 256 pixels, i.e. 8 blocks), taken by one warp, one pixel per lane; the queue
-// holds the blocks of every tile of every registered view, so many keyframes of uneven sizes
-// share one launch, and hands tiles out longest list first so that the last items are short.  Warps never wait for one another: each walks its tile's slice of the
-// sorted list (Sec. 3.2.1) 32 entries at a time -- every lane reads one entry's projection
-// record, tests whether the primitive's pixel rectangle meets the warp's block, and the lanes
-// that hit stage their primitive into the warp's shared-memory slots -- then the warp evaluates
-// only the staged primitives, in list order (front to back in the forward, back to front in the
-// backward); the entries that meet the block are queued and staged 32 at a time.  A warp leaves
-// its block as soon as all its pixels are saturated.
+// tile_h x tile_w = 256 pixels, i.e. 8 blocks), taken by one warp; the queue holds the blocks of
+// every tile of every registered view, so many keyframes of uneven sizes share one launch, and
+// hands tiles out longest list first so that the last items are short.  Warps never wait for
+// one another.  A warp walks its tile's slice of the sorted list (Sec. 3.2.1) 32 entries at a
+// time -- every lane reads one entry's projection record and tests whether the primitive's pixel
+// rectangle meets the warp's block -- and stages the entries that do, 32 at a time, into shared
+// memory.  A staged batch is then evaluated pair-parallel: the (primitive, pixel) candidates --
+// every pixel of the block inside a staged primitive's rectangle that is still live -- are
+// numbered primitive-major, and each round gives one candidate to every lane (a binary search
+// over the per-primitive prefix counts and a select of the pixel from the primitive's pixel
+// mask), so the intersection math runs on all 32 lanes whatever the primitives' footprints.
+// Each pixel's lane then composites that round's hits on it in list order (front to back in the
+// forward, back to front in the backward), fetching them from the candidate lanes by shuffle.
+// A warp leaves its block as soon as all its pixels are saturated.
 //
 // Numerics.  Each pixel ray is intersected with a splat as two planes h_x, h_y through the
 // sensor (Sec. 3.2.2, Eq. planes_to_splat; Supp. D.1): h_a = (h_x.b_a, h_x.b_b, h_x.b_c),
@@ -32,12 +37,16 @@
 //
 // Forward and backward evaluate a pair with the same explicitly rounded operations, so the
 // backward replays exactly the contributor set of the forward.  The backward recovers
-// T_k = T_{k+1} / (1 - alpha_k) from the final transmittance, keeps the suffix sums B_{d,k},
-// B_{n,k}, B_{o,k} of Supp. D.2, sums each primitive's 13 per-pixel terms over the warp (a
-// recursive-halving reduce-scatter; shared-memory atomics measured twice as slow) into the
-// primitive's slot, and the lane that staged the primitive rotates the slot back to the world
-// frame and issues four float4 atomics into a per-primitive accumulator (view independent, so
-// gradients of many views add up directly).
+// T_k = T_{k+1} / (1 - alpha_k) from the final transmittance and keeps the suffix sums B_{d,k},
+// B_{n,k}, B_{o,k} of Supp. D.2 in the pixel's lane; the pixel lane hands dL/dalpha_k and the
+// blending weight back to the candidate lane, which forms the pair's 13 geometric terms.  The
+// backward numbers candidates in groups of four lanes that share one primitive (a primitive's
+// pixels fill whole groups), so the terms are summed inside the group by two exchanges and added
+// into the staged primitive's shared-memory accumulator by at most four lanes per group (shared
+// float atomics where all lanes of a primitive meet measured 3x slower).  After the batch, the
+// lane that staged a primitive rotates its sums back to the world frame and issues four float4
+// atomics into a per-primitive accumulator (view independent, so gradients of many views add up
+// directly).
 
 #include "splat_internal.cuh"
 
@@ -47,13 +56,16 @@ namespace {
 constexpr float kLooseBox = 1.01f;   // margin of the binary32 pre-test
 constexpr int kWarps = kBlock / 32;  // warps per CTA (independent)
 constexpr int kBlocksPerTile = kBlock / 32;
+constexpr int kAcc = 13;             // per staged primitive: g_ba'(3) g_bb'(3) g_c'(3) g_n(3) g_o
+constexpr uint32_t kFull = 0xFFFFFFFFu;
 
-struct __align__(16) Staged {
-    float4 a;    // b_alpha' (tile frame), o
-    float4 b;    // b_beta' (tile frame), packed pixel rectangle (bits)
-    float4 c;    // c' = Q b_c, hi part (tile frame)
-    float4 lo;   // c' remainder
-    float4 n;    // normal (sensor frame)
+// A staged primitive, as four float4 rows (structure of arrays, so that lanes reading different
+// primitives spread over the banks):
+//   a: b_alpha' (tile frame), o        b: b_beta' (tile frame), packed pixel rectangle (bits)
+//   c: c' = Q b_c, hi part (tile frame); w: low part of c'_x
+//   n: normal (sensor frame); w: low part of c'_y
+struct SlotRef {
+    const float4 &a, &b, &c, &n;
 };
 
 struct Pix {
@@ -75,15 +87,15 @@ __device__ __forceinline__ float dot3e(float a0, float a1, float a2, float b0, f
 // low-order cross terms; the third product (sin theta0 sin dgamma times the vertical offset) is
 // small and taken in binary32.
 __device__ __forceinline__ float dot3_f2(float h0, float h1, float h2, float l0, float l1,
-                                         const float4 &c, const float4 &cl)
+                                         const float4 &c, float cl0, float cl1)
 {
     const float p0 = __fmul_rn(h0, c.x), e0 = __fmaf_rn(h0, c.x, -p0);
     const float p1 = __fmul_rn(h1, c.y), e1 = __fmaf_rn(h1, c.y, -p1);
     float s, t;
     two_sum(p0, p1, s, t);
     float err = __fadd_rn(__fadd_rn(e0, e1), t);
-    err = __fmaf_rn(h0, cl.x, err);
-    err = __fmaf_rn(h1, cl.y, err);
+    err = __fmaf_rn(h0, cl0, err);
+    err = __fmaf_rn(h1, cl1, err);
     err = __fmaf_rn(l0, c.x, err);
     err = __fmaf_rn(l1, c.y, err);
     err = __fmaf_rn(h2, c.z, err);
@@ -144,52 +156,137 @@ __device__ __forceinline__ uint32_t local_rect(const PairRec &rec, const TileInf
            (static_cast<uint32_t>(c_lo) << 16) | (static_cast<uint32_t>(c_hi) << 24);
 }
 
-__device__ __forceinline__ bool in_rect(uint32_t rect, int lr, int lc)
+// pixel mask of a rectangle over the 4 x 8 block with top-left (br, bc): bit 8 r + c for the
+// block's row r and column c
+__device__ __forceinline__ uint32_t pixel_mask(uint32_t rect, int br, int bc)
 {
     const int r_lo = rect & 0xFF, r_hi = (rect >> 8) & 0xFF;
     const int c_lo = (rect >> 16) & 0xFF, c_hi = rect >> 24;
-    return lr >= r_lo && lr <= r_hi && lc >= c_lo && lc <= c_hi;
+    const int ra = max(r_lo - br, 0), rb = min(r_hi - br, 3);
+    const int ca = max(c_lo - bc, 0), cb = min(c_hi - bc, 7);
+    if (ra > rb || ca > cb) return 0u;
+    const uint32_t cols = ((2u << cb) - 1u) & ~((1u << ca) - 1u);
+    const uint32_t rows = (0xFFFFFFFFu >> (8 * (3 - rb))) & (0xFFFFFFFFu << (8 * ra));
+    return (cols * 0x01010101u) & rows;
 }
 
-// does the rectangle overlap the 4 x 8 block with top-left (br, bc)?
-__device__ __forceinline__ bool rect_meets_block(uint32_t rect, int br, int bc)
+// position of the j-th (from 0) set bit of m; m has more than j set bits
+__device__ __forceinline__ int nth_bit(uint32_t m, int j)
 {
-    const int r_lo = rect & 0xFF, r_hi = (rect >> 8) & 0xFF;
-    const int c_lo = (rect >> 16) & 0xFF, c_hi = rect >> 24;
-    return r_lo <= br + 3 && r_hi >= br && c_lo <= bc + 7 && c_hi >= bc;
+    int pos = 0;
+    int c = __popc(m & 0xFFFFu);
+    if (j >= c) { j -= c; m >>= 16; pos += 16; }
+    c = __popc(m & 0xFFu);
+    if (j >= c) { j -= c; m >>= 8; pos += 8; }
+    c = __popc(m & 0xFu);
+    if (j >= c) { j -= c; m >>= 4; pos += 4; }
+    c = __popc(m & 0x3u);
+    if (j >= c) { j -= c; m >>= 2; pos += 2; }
+    if (j >= static_cast<int>(m & 1u)) pos += 1;
+    return pos;
 }
 
-struct Prim {
-    int64_t i;
-    float sa, sb;
-    bool flip;
+// the largest lane b with off_b <= t (off is non-decreasing over the lanes and off_0 = 0)
+__device__ __forceinline__ int search_lane(int off, int t)
+{
+    int b = 0;
+#pragma unroll
+    for (int step = 16; step > 0; step >>= 1) {
+        const int o = __shfl_sync(kFull, off, b + step);
+        b = o <= t ? b + step : b;
+    }
+    return b;
+}
+
+// mask of the lanes t whose value key_t equals this lane's index (5 ballots over the key bits)
+__device__ __forceinline__ uint32_t lanes_keyed_to_me(bool valid, int key, int lane)
+{
+    uint32_t m = __ballot_sync(kFull, valid);
+#pragma unroll
+    for (int k = 0; k < 5; ++k) {
+        const uint32_t b = __ballot_sync(kFull, (key >> k) & 1);
+        m &= ((lane >> k) & 1) ? b : ~b;
+    }
+    return m;
+}
+
+// inclusive warp prefix sum
+__device__ __forceinline__ int warp_incl_scan(int v, int lane)
+{
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int u = __shfl_up_sync(kFull, v, o);
+        if (lane >= o) v += u;
+    }
+    return v;
+}
+
+// Per-warp shared state: the staged batch (structure of arrays), the block's pixel frames
+// (structure of arrays, four float4 per pixel), and the queue of list entries that meet the
+// block and wait to be staged (appended in walk order 32 at a time).
+struct WarpBatch {
+    float4 a[32], b[32], c[32], n[32];
+    uint32_t pos[32];     // list position of the staged entry (backward: bit 31 = flipped)
+    uint32_t prim[32];    // primitive index
+    float4 p0[32], p1[32], p2[32], p3[32];
 };
 
-// stage pair id p of the tile into the tile frame
-__device__ __forceinline__ void stage(const RenderArgs &A, const TileInfo &ti, uint32_t p,
-                                      bool flip, uint32_t rect, Staged &out, Prim &pr)
+struct WarpQueue {
+    uint32_t p[64];      // pair id
+    uint32_t rect[64];   // pixel rectangle inside the tile
+    uint32_t pos[64];    // list position, bit 31: normal flipped
+};
+
+__device__ __forceinline__ SlotRef slot_at(const WarpBatch &w, int s)
+{
+    return SlotRef{w.a[s], w.b[s], w.c[s], w.n[s]};
+}
+
+__device__ __forceinline__ void put_pix(WarpBatch &w, int lane, const Pix &p)
+{
+    w.p0[lane] = make_float4(p.hx0, p.hx1, p.hx2, p.hy0);
+    w.p1[lane] = make_float4(p.hy1, p.hy2, p.v0, p.v1);
+    w.p2[lane] = make_float4(p.v2, p.hxl0, p.hxl1, p.hyl0);
+    w.p3[lane] = make_float4(p.hyl1, 0.0f, 0.0f, 0.0f);
+}
+
+__device__ __forceinline__ Pix get_pix(const WarpBatch &w, int l)
+{
+    const float4 a = w.p0[l], b = w.p1[l], c = w.p2[l], d = w.p3[l];
+    Pix p;
+    p.hx0 = a.x; p.hx1 = a.y; p.hx2 = a.z;
+    p.hy0 = a.w; p.hy1 = b.x; p.hy2 = b.y;
+    p.v0 = b.z; p.v1 = b.w; p.v2 = c.x;
+    p.hxl0 = c.y; p.hxl1 = c.z; p.hxl2 = 0.0f;
+    p.hyl0 = c.w; p.hyl1 = d.x; p.hyl2 = 0.0f;
+    return p;
+}
+
+// stage pair id p of the tile into slot s, in the tile frame; returns the primitive index
+__device__ __forceinline__ uint32_t stage(const RenderArgs &A, const TileInfo &ti, uint32_t p,
+                                          bool flip, uint32_t rect, WarpBatch &w, int s)
 {
     const int64_t i = static_cast<int64_t>(p) - static_cast<int64_t>(ti.view) * A.n;
     const float4 pl = A.pos_logit[i];
     const float4 q = A.quat[i];
     const float2 ls = A.log_scale[i];
     const float rn = rsqrtf(q.x * q.x + q.y * q.y + q.z * q.z + q.w * q.w);
-    const float w = q.x * rn, x = q.y * rn, y = q.z * rn, z = q.w * rn;
-    const float ta0 = 1.0f - 2.0f * (y * y + z * z), ta1 = 2.0f * (x * y + w * z),
-                ta2 = 2.0f * (x * z - w * y);
-    const float tb0 = 2.0f * (x * y - w * z), tb1 = 1.0f - 2.0f * (x * x + z * z),
-                tb2 = 2.0f * (y * z + w * x);
-    const float tn0 = 2.0f * (x * z + w * y), tn1 = 2.0f * (y * z - w * x),
+    const float qw = q.x * rn, x = q.y * rn, y = q.z * rn, z = q.w * rn;
+    const float ta0 = 1.0f - 2.0f * (y * y + z * z), ta1 = 2.0f * (x * y + qw * z),
+                ta2 = 2.0f * (x * z - qw * y);
+    const float tb0 = 2.0f * (x * y - qw * z), tb1 = 1.0f - 2.0f * (x * x + z * z),
+                tb2 = 2.0f * (y * z + qw * x);
+    const float tn0 = 2.0f * (x * z + qw * y), tn1 = 2.0f * (y * z - qw * x),
                 tn2 = 1.0f - 2.0f * (x * x + y * y);
     const float sa = __expf(ls.x), sb = __expf(ls.y);
     const float o = 1.0f / (1.0f + __expf(-pl.w));
     const float *M = ti.M_hi;
-    out.a = make_float4(sa * (M[0] * ta0 + M[1] * ta1 + M[2] * ta2),
-                        sa * (M[3] * ta0 + M[4] * ta1 + M[5] * ta2),
-                        sa * (M[6] * ta0 + M[7] * ta1 + M[8] * ta2), o);
-    out.b = make_float4(sb * (M[0] * tb0 + M[1] * tb1 + M[2] * tb2),
-                        sb * (M[3] * tb0 + M[4] * tb1 + M[5] * tb2),
-                        sb * (M[6] * tb0 + M[7] * tb1 + M[8] * tb2), __uint_as_float(rect));
+    w.a[s] = make_float4(sa * (M[0] * ta0 + M[1] * ta1 + M[2] * ta2),
+                         sa * (M[3] * ta0 + M[4] * ta1 + M[5] * ta2),
+                         sa * (M[6] * ta0 + M[7] * ta1 + M[8] * ta2), o);
+    w.b[s] = make_float4(sb * (M[0] * tb0 + M[1] * tb1 + M[2] * tb2),
+                         sb * (M[3] * tb0 + M[4] * tb1 + M[5] * tb2),
+                         sb * (M[6] * tb0 + M[7] * tb1 + M[8] * tb2), __uint_as_float(rect));
     f2 c[3];
 #pragma unroll
     for (int r = 0; r < 3; ++r)
@@ -197,17 +294,13 @@ __device__ __forceinline__ void stage(const RenderArgs &A, const TileInfo &ti, u
                             f2{ti.M_hi[3 * r + 1], ti.M_lo[3 * r + 1]},
                             f2{ti.M_hi[3 * r + 2], ti.M_lo[3 * r + 2]}, pl.x, pl.y, pl.z,
                             f2{ti.u_hi[r], ti.u_lo[r]});
-    out.c = make_float4(c[0].h, c[1].h, c[2].h, 0.0f);
-    out.lo = make_float4(c[0].l, c[1].l, c[2].l, 0.0f);
     const float *R = ti.R;
     const float fs = flip ? -1.0f : 1.0f;
-    out.n = make_float4(fs * (R[0] * tn0 + R[1] * tn1 + R[2] * tn2),
-                        fs * (R[3] * tn0 + R[4] * tn1 + R[5] * tn2),
-                        fs * (R[6] * tn0 + R[7] * tn1 + R[8] * tn2), 0.0f);
-    pr.i = i;
-    pr.sa = sa;
-    pr.sb = sb;
-    pr.flip = flip;
+    w.c[s] = make_float4(c[0].h, c[1].h, c[2].h, c[0].l);
+    w.n[s] = make_float4(fs * (R[0] * tn0 + R[1] * tn1 + R[2] * tn2),
+                         fs * (R[3] * tn0 + R[4] * tn1 + R[5] * tn2),
+                         fs * (R[6] * tn0 + R[7] * tn1 + R[8] * tn2), c[1].l);
+    return static_cast<uint32_t>(i);
 }
 
 struct Hit {
@@ -217,7 +310,7 @@ struct Hit {
 };
 
 // the per-pair test and geometry, identical in forward and backward
-__device__ __forceinline__ bool evaluate(const Staged &s, const Pix &px, float sigma,
+__device__ __forceinline__ bool evaluate(const SlotRef &s, const Pix &px, float sigma,
                                          float amin, float amax, Hit &h)
 {
     h.ha0 = dot3e(px.hx0, px.hx1, px.hx2, s.a.x, s.a.y, s.a.z);
@@ -234,8 +327,8 @@ __device__ __forceinline__ bool evaluate(const Staged &s, const Pix &px, float s
         !(fmaxf(fabsf(pxx), fabsf(pyy)) <= __fmul_rn(sigma * kLooseBox, apz)))
         return false;
     // precise lateral offsets of the centre from the two pixel planes
-    h.ha2 = dot3_f2(px.hx0, px.hx1, px.hx2, px.hxl0, px.hxl1, s.c, s.lo);
-    h.hb2 = dot3_f2(px.hy0, px.hy1, px.hy2, px.hyl0, px.hyl1, s.c, s.lo);
+    h.ha2 = dot3_f2(px.hx0, px.hx1, px.hx2, px.hxl0, px.hxl1, s.c, s.c.w, s.n.w);
+    h.hb2 = dot3_f2(px.hy0, px.hy1, px.hy2, px.hyl0, px.hyl1, s.c, s.c.w, s.n.w);
     h.px = __fmaf_rn(h.ha1, h.hb2, -__fmul_rn(h.ha2, h.hb1));
     h.py = __fmaf_rn(h.ha2, h.hb0, -__fmul_rn(h.ha0, h.hb2));
     if (!(fmaxf(fabsf(h.px), fabsf(h.py)) <= __fmul_rn(sigma, apz))) return false;
@@ -255,37 +348,11 @@ __device__ __forceinline__ bool evaluate(const Staged &s, const Pix &px, float s
     return h.d > 0.0f;
 }
 
-// Sum 16 per-lane values over the warp by recursive halving (a reduce-scatter): at each of 4
-// exchange steps a lane keeps half of its values and adds its partner's copy of that half, then
-// a fifth exchange completes the 32-lane sum.  Returns the total of value index
-// reduced_index(lane) -- 16 shuffles instead of 80 for a shuffle tree per value.
-__device__ __forceinline__ float warp_reduce16(float (&v)[16], int lane)
-{
-#pragma unroll
-    for (int s = 0; s < 4; ++s) {
-        const int m = 1 << s;
-        const int half = 8 >> s;
-        const bool up = (lane & m) != 0;
-#pragma unroll
-        for (int k = 0; k < half; ++k) {
-            const float send = up ? v[k] : v[k + half];
-            const float keep = up ? v[k + half] : v[k];
-            v[k] = keep + __shfl_xor_sync(0xFFFFFFFFu, send, m);
-        }
-    }
-    return v[0] + __shfl_xor_sync(0xFFFFFFFFu, v[0], 16);
-}
-
-__device__ __forceinline__ int reduced_index(int lane)
-{
-    return ((lane & 1) ? 8 : 0) + ((lane & 2) ? 4 : 0) + ((lane & 4) ? 2 : 0) + ((lane & 8) ? 1 : 0);
-}
-
 // add a per-lane counter to a global total: one atomic per warp, no block barrier
 __device__ __forceinline__ void warp_count(unsigned long long v, unsigned long long *total)
 {
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xFFFFFFFFu, v, o);
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
     if ((threadIdx.x & 31) == 0 && v) atomicAdd(total, v);
 }
 
@@ -294,7 +361,7 @@ __device__ __forceinline__ uint32_t next_item(uint32_t *queue, int lane)
 {
     uint32_t it = 0;
     if (lane == 0) it = atomicAdd(queue, 1u);
-    return __shfl_sync(0xFFFFFFFFu, it, 0);
+    return __shfl_sync(kFull, it, 0);
 }
 
 // copy the tile's 192-byte record into the warp's shared slot
@@ -329,19 +396,7 @@ __device__ __forceinline__ BlockPix block_pixel(const TileInfo &ti, int blk, int
     return b;
 }
 
-// ---------------------------------------------------------------------------------------------
-// forward
-// ---------------------------------------------------------------------------------------------
-// Per-warp queue of list entries relevant to the warp's block: entries are appended in list
-// order 32 at a time (one chunk per step) and staged 32 at a time, so one staging pass serves 32
-// primitives whatever the fraction of the list that meets the block.
-struct WarpQueue {
-    uint32_t p[64];      // pair id
-    uint32_t rect[64];   // pixel rectangle inside the tile
-    uint32_t pos[64];    // list position, bit 31: normal flipped
-};
-
-// read one chunk entry per lane: pair id, rectangle, whether it meets the block
+// read one list entry per lane: pair id, rectangle, whether it meets the block
 template <int TH, int TW>
 __device__ __forceinline__ bool read_entry(const RenderArgs &A, const TileInfo &ti, uint32_t j,
                                            const BlockPix &bp, uint32_t &p, uint32_t &rect,
@@ -351,24 +406,80 @@ __device__ __forceinline__ bool read_entry(const RenderArgs &A, const TileInfo &
     const PairRec rec = A.recs[p];
     rect = local_rect<TH, TW>(rec, ti);
     flip = (rec.cf & kPairFlip) != 0;
-    return rect_meets_block(rect, bp.br, bp.bc);
+    return pixel_mask(rect, bp.br, bp.bc) != 0u;
+}
+
+// Candidate numbering of a staged batch: lane b holds its primitive's live-pixel mask m, the
+// count before it (off) and, after the call, the batch total K (uniform).
+struct Numbering {
+    uint32_t m;
+    int off, K;
+};
+
+__device__ __forceinline__ Numbering number_candidates(uint32_t m, int lane)
+{
+    Numbering nb;
+    nb.m = m;
+    const int n = __popc(m);
+    const int incl = warp_incl_scan(n, lane);
+    nb.off = incl - n;
+    nb.K = __shfl_sync(kFull, incl, 31);
+    return nb;
+}
+
+// candidate t of the batch: its primitive's slot b and its pixel l (meaningful when t < K)
+__device__ __forceinline__ void candidate(const Numbering &nb, int t, int &b, int &l)
+{
+    b = search_lane(nb.off, t);
+    const uint32_t mb = __shfl_sync(kFull, nb.m, b);
+    const int j = t - __shfl_sync(kFull, nb.off, b);
+    l = nth_bit(mb, j < 0 ? 0 : j);
+}
+
+// The backward numbers groups of four candidates instead: a primitive's pixels fill
+// ceil(n / 4) whole groups (off and K count groups), so that the four lanes of an aligned lane
+// group always belong to one primitive and its terms can be summed inside the group.
+__device__ __forceinline__ Numbering number_groups(uint32_t m, int lane)
+{
+    Numbering nb;
+    nb.m = m;
+    const int n = (__popc(m) + 3) >> 2;
+    const int incl = warp_incl_scan(n, lane);
+    nb.off = incl - n;
+    nb.K = __shfl_sync(kFull, incl, 31);
+    return nb;
+}
+
+// member q (0..3) of candidate group u: slot b, pixel l, and whether it is a candidate
+__device__ __forceinline__ bool group_member(const Numbering &nb, int u, int q, int &b, int &l)
+{
+    b = search_lane(nb.off, u);
+    const uint32_t mb = __shfl_sync(kFull, nb.m, b);
+    const int j = 4 * (u - __shfl_sync(kFull, nb.off, b)) + q;
+    const bool valid = u < nb.K && j >= 0 && j < __popc(mb);
+    l = nth_bit(mb, valid ? j : 0);
+    return valid;
 }
 
 // ---------------------------------------------------------------------------------------------
 // forward
 // ---------------------------------------------------------------------------------------------
+struct FwdShared {
+    WarpBatch w[kWarps];
+    TileInfo ti[kWarps];
+    WarpQueue q[kWarps];
+};
+
 template <int TH, int TW>
 __global__ void __launch_bounds__(kBlock, 3) k_render_fwd(const RenderArgs A)
 {
     static_assert(TH * TW == kBlock && TH % 4 == 0 && TW % 8 == 0, "4x8 warp blocks");
-    __shared__ Staged s_st[kWarps][32];
-    __shared__ TileInfo s_ti[kWarps];
-    __shared__ WarpQueue s_q[kWarps];
+    __shared__ FwdShared sh;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const uint32_t lt_mask = (1u << lane) - 1u;
-    Staged *slots = s_st[warp];
-    TileInfo &ti = s_ti[warp];
-    WarpQueue &q = s_q[warp];
+    WarpBatch &w = sh.w[warp];
+    TileInfo &ti = sh.ti[warp];
+    WarpQueue &q = sh.q[warp];
     unsigned long long evals = 0;
 
     for (;;) {
@@ -379,51 +490,75 @@ __global__ void __launch_bounds__(kBlock, 3) k_render_fwd(const RenderArgs A)
         __syncwarp();
         load_tile(A.tiles, tile, ti, lane);
         const BlockPix bp = block_pixel<TH, TW>(ti, blk, lane);
-        const Pix px = load_pix(A.pixframes, bp.inside ? bp.pf : ti.pix_base);
+        put_pix(w, lane, load_pix(A.pixframes, bp.inside ? bp.pf : ti.pix_base));
         const uint2 rg = A.ranges[tile];
         float T = 1.0f, D = 0.0f, N0 = 0.0f, N1 = 0.0f, N2 = 0.0f, O = 0.0f;
         int last = 0;
         bool done = !bp.inside;
 
-        // stage queue entries [0, cnt) and composite them in list order
+        // stage queue entries [0, cnt) and composite them, round by round
         auto composite = [&](int cnt) {
+            uint32_t m = 0u;
             if (lane < cnt) {
-                Prim pr;
-                stage(A, ti, q.p[lane], (q.pos[lane] >> 31) != 0, q.rect[lane], slots[lane], pr);
+                stage(A, ti, q.p[lane], (q.pos[lane] >> 31) != 0, q.rect[lane], w, lane);
+                w.pos[lane] = q.pos[lane] & 0x7FFFFFFFu;
+                m = pixel_mask(q.rect[lane], bp.br, bp.bc);
             }
+            m &= __ballot_sync(kFull, !done);
+            const Numbering nb = number_candidates(m, lane);
             __syncwarp();
-            for (int b = 0; b < cnt; ++b) {
-                const Staged &s = slots[b];
-                if (done || !in_rect(__float_as_uint(s.b.w), bp.lr, bp.lc)) continue;
-                ++evals;
+            for (int r0 = 0; r0 < nb.K; r0 += 32) {
+                const int t = r0 + lane;
+                const bool valid = t < nb.K;
+                int b, l;
+                candidate(nb, t, b, l);
                 Hit h;
-                if (!evaluate(s, px, A.sigma, A.alpha_min, A.alpha_max, h)) continue;
-                const float tt = __fmul_rn(T, __fsub_rn(1.0f, h.a));
-                if (tt < A.t_min) {
-                    done = true;
-                    continue;
+                h.a = h.d = 0.0f;
+                bool hit = false;
+                if (valid) {
+                    ++evals;
+                    hit = evaluate(slot_at(w, b), get_pix(w, l), A.sigma, A.alpha_min,
+                                   A.alpha_max, h);
                 }
-                const float w = __fmul_rn(h.a, T);
-                D = __fmaf_rn(w, h.d, D);
-                const float4 nn = s.n;
-                N0 = __fmaf_rn(w, nn.x, N0);
-                N1 = __fmaf_rn(w, nn.y, N1);
-                N2 = __fmaf_rn(w, nn.z, N2);
-                O = __fadd_rn(O, w);
-                T = tt;
-                last = static_cast<int>(q.pos[b] & 0x7FFFFFFFu) + 1;
+                // this pixel's hits of the round, in list order, fetched from their lanes
+                uint32_t mine = lanes_keyed_to_me(hit, l, lane);
+                while (__any_sync(kFull, mine != 0u)) {
+                    const bool have = mine != 0u;
+                    const int src = have ? __ffs(mine) - 1 : lane;
+                    mine &= mine - 1u;
+                    const float a = __shfl_sync(kFull, h.a, src);
+                    const float d = __shfl_sync(kFull, h.d, src);
+                    const int bs = __shfl_sync(kFull, b, src);
+                    if (have && !done) {
+                        const float tt = __fmul_rn(T, __fsub_rn(1.0f, a));
+                        if (tt < A.t_min) {
+                            done = true;
+                        } else {
+                            const float wgt = __fmul_rn(a, T);
+                            D = __fmaf_rn(wgt, d, D);
+                            const float4 nn = w.n[bs];
+                            N0 = __fmaf_rn(wgt, nn.x, N0);
+                            N1 = __fmaf_rn(wgt, nn.y, N1);
+                            N2 = __fmaf_rn(wgt, nn.z, N2);
+                            O = __fadd_rn(O, wgt);
+                            T = tt;
+                            last = static_cast<int>(w.pos[bs]) + 1;
+                        }
+                    }
+                }
+                if (__all_sync(kFull, done)) break;
             }
             __syncwarp();
         };
 
         int qn = 0;
         for (uint32_t ch = rg.x; ch < rg.y; ch += 32) {
-            if (__all_sync(0xFFFFFFFFu, done)) break;
+            if (__all_sync(kFull, done)) break;
             const uint32_t j = ch + lane;
             bool rel = false, flip = false;
             uint32_t p = 0, rect = 0;
             if (j < rg.y) rel = read_entry<TH, TW>(A, ti, j, bp, p, rect, flip);
-            const uint32_t m = __ballot_sync(0xFFFFFFFFu, rel);
+            const uint32_t m = __ballot_sync(kFull, rel);
             if (rel) {
                 const int pos = qn + __popc(m & lt_mask);
                 q.p[pos] = p;
@@ -443,7 +578,7 @@ __global__ void __launch_bounds__(kBlock, 3) k_render_fwd(const RenderArgs A)
                 __syncwarp();
             }
         }
-        if (qn > 0 && !__all_sync(0xFFFFFFFFu, done)) composite(qn);
+        if (qn > 0 && !__all_sync(kFull, done)) composite(qn);
         if (bp.inside) {
             A.depth[bp.out] = D;
             A.normal[bp.out] = N0;
@@ -460,22 +595,27 @@ __global__ void __launch_bounds__(kBlock, 3) k_render_fwd(const RenderArgs A)
 // ---------------------------------------------------------------------------------------------
 // backward
 // ---------------------------------------------------------------------------------------------
-constexpr int kAcc = 16;   // per staged primitive: g_ba'(3) g_bb'(3) g_c'(3) g_n(3) g_o, pad
+struct BwdShared {
+    WarpBatch w[kWarps];
+    float acc[kWarps][32][kAcc];
+    float2 gw[kWarps][32];   // per candidate lane: (dL/dalpha, blending weight) from its pixel
+    TileInfo ti[kWarps];
+    WarpQueue q[kWarps];
+};
 
 template <int TH, int TW>
 __global__ void __launch_bounds__(kBlock, 3) k_render_bwd(const RenderArgs A)
 {
     static_assert(TH * TW == kBlock && TH % 4 == 0 && TW % 8 == 0, "4x8 warp blocks");
-    __shared__ Staged s_st[kWarps][32];
-    __shared__ float s_acc[kWarps][32][kAcc];
-    __shared__ TileInfo s_ti[kWarps];
-    __shared__ WarpQueue s_q[kWarps];
+    extern __shared__ __align__(16) unsigned char s_raw[];
+    BwdShared &sh = *reinterpret_cast<BwdShared *>(s_raw);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const uint32_t gt_mask = ~((2u << lane) - 1u);   // lanes above this one
-    Staged *slots = s_st[warp];
-    float(*acc)[kAcc] = s_acc[warp];
-    TileInfo &ti = s_ti[warp];
-    WarpQueue &q = s_q[warp];
+    WarpBatch &w = sh.w[warp];
+    float(*acc)[kAcc] = sh.acc[warp];
+    float2 *gwl = sh.gw[warp];
+    TileInfo &ti = sh.ti[warp];
+    WarpQueue &q = sh.q[warp];
     unsigned long long evals = 0;
 
     for (;;) {
@@ -486,7 +626,7 @@ __global__ void __launch_bounds__(kBlock, 3) k_render_bwd(const RenderArgs A)
         __syncwarp();
         load_tile(A.tiles, tile, ti, lane);
         const BlockPix bp = block_pixel<TH, TW>(ti, blk, lane);
-        const Pix px = load_pix(A.pixframes, bp.inside ? bp.pf : ti.pix_base);
+        put_pix(w, lane, load_pix(A.pixframes, bp.inside ? bp.pf : ti.pix_base));
         const uint2 rg = A.ranges[tile];
         float T = 1.0f, gD = 0.0f, gN0 = 0.0f, gN1 = 0.0f, gN2 = 0.0f, gO = 0.0f;
         int nl = 0;
@@ -505,117 +645,165 @@ __global__ void __launch_bounds__(kBlock, 3) k_render_bwd(const RenderArgs A)
         // the warp's bound: nothing at or past it contributes to any of its pixels
         int wl = nl;
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) wl = max(wl, __shfl_xor_sync(0xFFFFFFFFu, wl, o));
+        for (int o = 16; o > 0; o >>= 1) wl = max(wl, __shfl_xor_sync(kFull, wl, o));
+        const uint32_t live = __ballot_sync(kFull, nl > 0);
 
         // stage queue entries [0, cnt) (in decreasing list order), replay and differentiate them
-        // back to front, then flush each staged primitive's sums (lane b flushes slot b)
+        // round by round, then flush each staged primitive's sums (lane b flushes slot b)
         auto adjoint = [&](int cnt) {
-            Prim pr;
-            pr.i = -1;
+            uint32_t m = 0u;
             if (lane < cnt) {
-                stage(A, ti, q.p[lane], (q.pos[lane] >> 31) != 0, q.rect[lane], slots[lane], pr);
+                w.prim[lane] = stage(A, ti, q.p[lane], (q.pos[lane] >> 31) != 0, q.rect[lane],
+                                     w, lane);
+                w.pos[lane] = q.pos[lane];
 #pragma unroll
-                for (int j = 0; j < kAcc; ++j) acc[lane][j] = 0.0f;
+                for (int c = 0; c < kAcc; ++c) acc[lane][c] = 0.0f;
+                m = pixel_mask(q.rect[lane], bp.br, bp.bc) & live;
             }
+            const Numbering nb = number_groups(m, lane);
             __syncwarp();
-            for (int b = 0; b < cnt; ++b) {
-                const int k = static_cast<int>(q.pos[b] & 0x7FFFFFFFu);
-                const Staged &s = slots[b];
-                float g[16];
-#pragma unroll
-                for (int c = 0; c < 16; ++c) g[c] = 0.0f;
-                bool contrib = false;
-                if (k < nl && in_rect(__float_as_uint(s.b.w), bp.lr, bp.lc)) {
+            for (int u0 = 0; u0 < nb.K; u0 += 8) {
+                int b, l;
+                const bool valid = group_member(nb, u0 + (lane >> 2), lane & 3, b, l);
+                const int k = static_cast<int>(w.pos[b] & 0x7FFFFFFFu);
+                const int nl_l = __shfl_sync(kFull, nl, l);
+                Hit h;
+                h.a = h.d = 0.0f;
+                h.clamped = false;
+                bool hit = false;
+                if (valid && k < nl_l) {
                     ++evals;
-                    Hit h;
-                    if (evaluate(s, px, A.sigma, A.alpha_min, A.alpha_max, h)) {
-                        contrib = true;
-                        const float om = __fsub_rn(1.0f, h.a);
-                        const float inv_om = __fdividef(1.0f, om);
+                    hit = evaluate(slot_at(w, b), get_pix(w, l), A.sigma, A.alpha_min,
+                                   A.alpha_max, h);
+                }
+                // each pixel lane walks its hits of the round back to front: transmittance,
+                // suffix sums, and dL/dalpha_k with the weight handed back to the hit's lane
+                uint32_t mine = lanes_keyed_to_me(hit, l, lane);
+                while (__any_sync(kFull, mine != 0u)) {
+                    const bool have = mine != 0u;
+                    const int src = have ? __ffs(mine) - 1 : lane;
+                    mine &= mine - 1u;
+                    const float a = __shfl_sync(kFull, h.a, src);
+                    const float d = __shfl_sync(kFull, h.d, src);
+                    const int bc = __shfl_sync(kFull, b | (h.clamped ? 0x100 : 0), src);
+                    if (have) {
+                        const float inv_om = __fdividef(1.0f, __fsub_rn(1.0f, a));
                         const float Tk = T * inv_om;
-                        const float w = __fmul_rn(h.a, Tk);
-                        const float4 nn = s.n;
+                        const float wgt = __fmul_rn(a, Tk);
+                        const float4 nn = w.n[bc & 0xFF];
                         // dL/dalpha_k = sum_ch g_ch (x_k A_k - B_ch,k / (1 - alpha_k))
-                        float gA = gD * (h.d * Tk - Bd * inv_om);
+                        float gA = gD * (d * Tk - Bd * inv_om);
                         gA += gO * (Tk - Bo * inv_om);
                         gA += gN0 * (nn.x * Tk - Bn0 * inv_om);
                         gA += gN1 * (nn.y * Tk - Bn1 * inv_om);
                         gA += gN2 * (nn.z * Tk - Bn2 * inv_om);
-                        Bd += w * h.d;
-                        Bo += w;
-                        Bn0 += w * nn.x;
-                        Bn1 += w * nn.y;
-                        Bn2 += w * nn.z;
+                        Bd += wgt * d;
+                        Bo += wgt;
+                        Bn0 += wgt * nn.x;
+                        Bn1 += wgt * nn.y;
+                        Bn2 += wgt * nn.z;
                         T = Tk;
-                        const float gd = gD * w;          // dL/dd_k
-                        g[9] = gN0 * w;                    // dL/dn_k
-                        g[10] = gN1 * w;
-                        g[11] = gN2 * w;
-                        const float gAe = h.clamped ? 0.0f : gA;
-                        g[12] = gAe * h.G;                 // dL/do
-                        // dL/ds_hat: density term and range term (d = nu . v)
-                        const float vba = px.v0 * s.a.x + px.v1 * s.a.y + px.v2 * s.a.z;
-                        const float vbb = px.v0 * s.b.x + px.v1 * s.b.y + px.v2 * s.b.z;
-                        const float gsa = -gAe * h.a * h.sa + gd * vba;
-                        const float gsb = -gAe * h.a * h.sb + gd * vbb;
-                        // dL/dp_hat with s_hat = (p_x, p_y) / p_z
-                        const float gp0 = gsa * h.inv, gp1 = gsb * h.inv;
-                        const float gp2 = -(h.sa * gsa + h.sb * gsb) * h.inv;
-                        // rho_a = g_p x h_a = dL/dh_b ; rho_b = g_p x h_b = -dL/dh_a
-                        const float ra0 = gp1 * h.ha2 - gp2 * h.ha1;
-                        const float ra1 = gp2 * h.ha0 - gp0 * h.ha2;
-                        const float ra2 = gp0 * h.ha1 - gp1 * h.ha0;
-                        const float rb0 = gp1 * h.hb2 - gp2 * h.hb1;
-                        const float rb1 = gp2 * h.hb0 - gp0 * h.hb2;
-                        const float rb2 = gp0 * h.hb1 - gp1 * h.hb0;
-                        const float t0 = gd * h.sa, t1 = gd * h.sb;
-                        g[0] = -rb0 * px.hx0 + ra0 * px.hy0 + t0 * px.v0;
-                        g[1] = -rb0 * px.hx1 + ra0 * px.hy1 + t0 * px.v1;
-                        g[2] = -rb0 * px.hx2 + ra0 * px.hy2 + t0 * px.v2;
-                        g[3] = -rb1 * px.hx0 + ra1 * px.hy0 + t1 * px.v0;
-                        g[4] = -rb1 * px.hx1 + ra1 * px.hy1 + t1 * px.v1;
-                        g[5] = -rb1 * px.hx2 + ra1 * px.hy2 + t1 * px.v2;
-                        g[6] = -rb2 * px.hx0 + ra2 * px.hy0 + gd * px.v0;
-                        g[7] = -rb2 * px.hx1 + ra2 * px.hy1 + gd * px.v1;
-                        g[8] = -rb2 * px.hx2 + ra2 * px.hy2 + gd * px.v2;
+                        gwl[src] = make_float2((bc & 0x100) ? 0.0f : gA, wgt);
                     }
                 }
-                const uint32_t cm = __ballot_sync(0xFFFFFFFFu, contrib);
-                if (cm == 0u) continue;
-                if ((cm & (cm - 1u)) == 0u) {   // a single contributing lane: a plain add
-                    if (contrib) {
+                const float gDl = __shfl_sync(kFull, gD, l);
+                const float gNl0 = __shfl_sync(kFull, gN0, l);
+                const float gNl1 = __shfl_sync(kFull, gN1, l);
+                const float gNl2 = __shfl_sync(kFull, gN2, l);
+                __syncwarp();
+                float g[16];
 #pragma unroll
-                        for (int c = 0; c < 13; ++c) acc[b][c] += g[c];
-                    }
-                } else {
-                    const float tot = warp_reduce16(g, lane);
-                    const int c = reduced_index(lane);
-                    if (lane < 16 && c < 13) acc[b][c] += tot;
+                for (int c = 0; c < 16; ++c) g[c] = 0.0f;
+                if (hit) {
+                    const float2 gw = gwl[lane];
+                    const float gAe = gw.x, wgt = gw.y;
+                    const SlotRef st = slot_at(w, b);
+                    const Pix px = get_pix(w, l);
+                    const float gd = gDl * wgt;            // dL/dd_k
+                    g[9] = gNl0 * wgt;                      // dL/dn_k
+                    g[10] = gNl1 * wgt;
+                    g[11] = gNl2 * wgt;
+                    g[12] = gAe * h.G;                      // dL/do
+                    // dL/ds_hat: density term and range term (d = nu . v)
+                    const float vba = px.v0 * st.a.x + px.v1 * st.a.y + px.v2 * st.a.z;
+                    const float vbb = px.v0 * st.b.x + px.v1 * st.b.y + px.v2 * st.b.z;
+                    const float gsa = -gAe * h.a * h.sa + gd * vba;
+                    const float gsb = -gAe * h.a * h.sb + gd * vbb;
+                    // dL/dp_hat with s_hat = (p_x, p_y) / p_z
+                    const float gp0 = gsa * h.inv, gp1 = gsb * h.inv;
+                    const float gp2 = -(h.sa * gsa + h.sb * gsb) * h.inv;
+                    // rho_a = g_p x h_a = dL/dh_b ; rho_b = g_p x h_b = -dL/dh_a
+                    const float ra0 = gp1 * h.ha2 - gp2 * h.ha1;
+                    const float ra1 = gp2 * h.ha0 - gp0 * h.ha2;
+                    const float ra2 = gp0 * h.ha1 - gp1 * h.ha0;
+                    const float rb0 = gp1 * h.hb2 - gp2 * h.hb1;
+                    const float rb1 = gp2 * h.hb0 - gp0 * h.hb2;
+                    const float rb2 = gp0 * h.hb1 - gp1 * h.hb0;
+                    const float t0 = gd * h.sa, t1 = gd * h.sb;
+                    g[0] = -rb0 * px.hx0 + ra0 * px.hy0 + t0 * px.v0;
+                    g[1] = -rb0 * px.hx1 + ra0 * px.hy1 + t0 * px.v1;
+                    g[2] = -rb0 * px.hx2 + ra0 * px.hy2 + t0 * px.v2;
+                    g[3] = -rb1 * px.hx0 + ra1 * px.hy0 + t1 * px.v0;
+                    g[4] = -rb1 * px.hx1 + ra1 * px.hy1 + t1 * px.v1;
+                    g[5] = -rb1 * px.hx2 + ra1 * px.hy2 + t1 * px.v2;
+                    g[6] = -rb2 * px.hx0 + ra2 * px.hy0 + gd * px.v0;
+                    g[7] = -rb2 * px.hx1 + ra2 * px.hy1 + gd * px.v1;
+                    g[8] = -rb2 * px.hx2 + ra2 * px.hy2 + gd * px.v2;
                 }
+                // sum the group's four lanes (one primitive) by recursive halving: after the
+                // exchange across lane bit 0 a lane keeps 8 of the 16 values, after bit 1 it
+                // keeps 4; groups of one primitive in the same round meet in the atomics
+                const uint32_t hm = __ballot_sync(kFull, hit);
+                if (hm != 0u) {
+#pragma unroll
+                    for (int c = 0; c < 8; ++c) {
+                        const bool up = (lane & 1) != 0;
+                        const float send = up ? g[c] : g[c + 8];
+                        const float keep = up ? g[c + 8] : g[c];
+                        g[c] = keep + __shfl_xor_sync(kFull, send, 1);
+                    }
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) {
+                        const bool up = (lane & 2) != 0;
+                        const float send = up ? g[c] : g[c + 4];
+                        const float keep = up ? g[c + 4] : g[c];
+                        g[c] = keep + __shfl_xor_sync(kFull, send, 2);
+                    }
+                    if ((hm >> (lane & ~3)) & 0xFu) {
+                        const int base = ((lane & 1) ? 8 : 0) + ((lane & 2) ? 4 : 0);
+#pragma unroll
+                        for (int c = 0; c < 4; ++c)
+                            if (base + c < kAcc) atomicAdd(&acc[b][base + c], g[c]);
+                    }
+                }
+                __syncwarp();
             }
-            __syncwarp();
             if (lane < cnt) {
                 const float *a = acc[lane];
                 bool any = false;
 #pragma unroll
-                for (int c = 0; c < 13; ++c) any |= a[c] != 0.0f;
+                for (int c = 0; c < kAcc; ++c) any |= a[c] != 0.0f;
                 if (any) {
                     const float *M = ti.M_hi;
                     const float *R = ti.R;
-                    const Staged &s = slots[lane];
+                    const SlotRef st = slot_at(w, lane);
+                    // the scales are the lengths of the staged axes (M is a rotation)
+                    const float sa = sqrtf(st.a.x * st.a.x + st.a.y * st.a.y + st.a.z * st.a.z);
+                    const float sb = sqrtf(st.b.x * st.b.x + st.b.y * st.b.y + st.b.z * st.b.z);
+                    const bool flip = (w.pos[lane] >> 31) != 0;
                     // world frame: M^T g' (M = Q R^c_w), normals: R^c_w^T g_n
                     float gmu[3], gta[3], gtb[3], gtn[3];
 #pragma unroll
                     for (int j = 0; j < 3; ++j) {
                         gmu[j] = M[j] * a[6] + M[3 + j] * a[7] + M[6 + j] * a[8];
-                        gta[j] = pr.sa * (M[j] * a[0] + M[3 + j] * a[1] + M[6 + j] * a[2]);
-                        gtb[j] = pr.sb * (M[j] * a[3] + M[3 + j] * a[4] + M[6 + j] * a[5]);
+                        gta[j] = sa * (M[j] * a[0] + M[3 + j] * a[1] + M[6 + j] * a[2]);
+                        gtb[j] = sb * (M[j] * a[3] + M[3 + j] * a[4] + M[6 + j] * a[5]);
                         gtn[j] = R[j] * a[9] + R[3 + j] * a[10] + R[6 + j] * a[11];
-                        if (pr.flip) gtn[j] = -gtn[j];
+                        if (flip) gtn[j] = -gtn[j];
                     }
-                    const float gls_a = a[0] * s.a.x + a[1] * s.a.y + a[2] * s.a.z;
-                    const float gls_b = a[3] * s.b.x + a[4] * s.b.y + a[5] * s.b.z;
-                    float4 *dst = A.wgrad + 4 * pr.i;
+                    const float gls_a = a[0] * st.a.x + a[1] * st.a.y + a[2] * st.a.z;
+                    const float gls_b = a[3] * st.b.x + a[4] * st.b.y + a[5] * st.b.z;
+                    float4 *dst = A.wgrad + 4 * static_cast<int64_t>(w.prim[lane]);
                     atomicAdd(dst + 0, make_float4(gmu[0], gmu[1], gmu[2], a[12]));
                     atomicAdd(dst + 1, make_float4(gta[0], gta[1], gta[2], gls_a));
                     atomicAdd(dst + 2, make_float4(gtb[0], gtb[1], gtb[2], gls_b));
@@ -631,7 +819,7 @@ __global__ void __launch_bounds__(kBlock, 3) k_render_bwd(const RenderArgs A)
             bool rel = false, flip = false;
             uint32_t p = 0, rect = 0;
             if (jl < wl) rel = read_entry<TH, TW>(A, ti, rg.x + jl, bp, p, rect, flip);
-            const uint32_t m = __ballot_sync(0xFFFFFFFFu, rel);
+            const uint32_t m = __ballot_sync(kFull, rel);
             if (rel) {   // queue in decreasing list position: higher lanes first
                 const int pos = qn + __popc(m & gt_mask);
                 q.p[pos] = p;
@@ -699,11 +887,24 @@ cudaError_t launch_render_fwd(const RenderArgs &a, int tile_h, int tile_w, int g
     });
 }
 
+// the backward's shared memory is above the 48 KB static limit: allow it once per instantiation
+template <int TH, int TW>
+cudaError_t bwd_prepare()
+{
+    static cudaError_t e = cudaFuncSetAttribute(k_render_bwd<TH, TW>,
+                                                cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                static_cast<int>(sizeof(BwdShared)));
+    return e;
+}
+
 cudaError_t launch_render_bwd(const RenderArgs &a, int tile_h, int tile_w, int grid,
                               cudaStream_t st)
 {
     return dispatch(tile_h, tile_w, [&](auto TH, auto TW) {
-        k_render_bwd<decltype(TH)::value, decltype(TW)::value><<<grid, kBlock, 0, st>>>(a);
+        constexpr int h = decltype(TH)::value, w = decltype(TW)::value;
+        const cudaError_t e = bwd_prepare<h, w>();
+        if (e != cudaSuccess) return e;
+        k_render_bwd<h, w><<<grid, kBlock, sizeof(BwdShared), st>>>(a);
         return cudaGetLastError();
     });
 }
@@ -713,8 +914,12 @@ int render_occupancy(int tile_h, int tile_w, bool backward)
     int blocks = 0;
     dispatch(tile_h, tile_w, [&](auto TH, auto TW) {
         constexpr int h = decltype(TH)::value, w = decltype(TW)::value;
-        if (backward)
-            return cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k_render_bwd<h, w>, kBlock, 0);
+        if (backward) {
+            const cudaError_t e = bwd_prepare<h, w>();
+            if (e != cudaSuccess) return e;
+            return cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k_render_bwd<h, w>,
+                                                                 kBlock, sizeof(BwdShared));
+        }
         return cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k_render_fwd<h, w>, kBlock, 0);
     });
     return blocks > 0 ? blocks : 1;
