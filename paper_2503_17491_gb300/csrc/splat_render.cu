@@ -41,9 +41,10 @@
 // B_{n,k}, B_{o,k} of Supp. D.2 in the pixel's lane; the pixel lane hands dL/dalpha_k and the
 // blending weight back to the candidate lane, which forms the pair's 13 geometric terms.  The
 // backward numbers candidates in groups of four lanes that share one primitive (a primitive's
-// pixels fill whole groups), so the terms are summed inside the group by two exchanges and added
-// into the staged primitive's shared-memory accumulator by at most four lanes per group (shared
-// float atomics where all lanes of a primitive meet measured 3x slower).  After the batch, the
+// pixels fill whole groups), so the terms are summed inside the group by two exchanges, then
+// across the consecutive groups of one primitive by a segmented suffix sum, and the primitive's
+// first group adds them into its shared-memory accumulator without atomics (shared float atomics
+// where the lanes of a primitive meet measured 3x slower).  After the batch, the
 // lane that staged a primitive rotates its sums back to the world frame and issues four float4
 // atomics into a per-primitive accumulator (view independent, so gradients of many views add up
 // directly).
@@ -208,6 +209,33 @@ __device__ __forceinline__ uint32_t lanes_keyed_to_me(bool valid, int key, int l
         m &= ((lane >> k) & 1) ? b : ~b;
     }
     return m;
+}
+
+// For slots ordered by strictly decreasing list position k_b (lanes b >= cnt pass k = -1) and a
+// bound nl per pixel lane: the mask of pixel lanes l with k_b < nl_l, returned to lane b.  Each
+// pixel finds how many leading slots lie at or past its bound (a binary search), and lane b
+// compares all 32 counts with b at once, bit-sliced over the counts' six bits.
+__device__ __forceinline__ uint32_t pixels_before_bound(int k, int nl, int b)
+{
+    int t = 0;
+#pragma unroll
+    for (int step = 16; step > 0; step >>= 1) {
+        const int kk = __shfl_sync(kFull, k, t + step - 1);
+        t = kk >= nl ? t + step : t;
+    }
+    t += __shfl_sync(kFull, k, 31) >= nl && t == 31 ? 1 : 0;
+    uint32_t lt = 0u, eq = kFull;
+#pragma unroll
+    for (int s = 5; s >= 0; --s) {
+        const uint32_t bits = __ballot_sync(kFull, (t >> s) & 1);
+        if ((b >> s) & 1) {
+            lt |= eq & ~bits;
+            eq &= bits;
+        } else {
+            eq &= ~bits;
+        }
+    }
+    return lt | eq;   // pixels whose count t_l <= b
 }
 
 // inclusive warp prefix sum
@@ -641,7 +669,7 @@ __global__ void __launch_bounds__(kBlock, 3) k_render_bwd(const RenderArgs A)
             }
             if (A.g_alpha) gO = A.g_alpha[bp.out];
         }
-        float Bd = 0.0f, Bo = 0.0f, Bn0 = 0.0f, Bn1 = 0.0f, Bn2 = 0.0f;
+        float Y = 0.0f;   // sum over channels of g_ch B_ch (suffix sums of Supp. D.2)
         // the warp's bound: nothing at or past it contributes to any of its pixels
         int wl = nl;
 #pragma unroll
@@ -660,6 +688,9 @@ __global__ void __launch_bounds__(kBlock, 3) k_render_bwd(const RenderArgs A)
                 for (int c = 0; c < kAcc; ++c) acc[lane][c] = 0.0f;
                 m = pixel_mask(q.rect[lane], bp.br, bp.bc) & live;
             }
+            // a pixel takes part only in slots before its last contributor
+            m &= pixels_before_bound(lane < cnt ? static_cast<int>(q.pos[lane] & 0x7FFFFFFFu) : -1,
+                                     nl, lane);
             const Numbering nb = number_groups(m, lane);
             __syncwarp();
             for (int u0 = 0; u0 < nb.K; u0 += 8) {
@@ -676,47 +707,47 @@ __global__ void __launch_bounds__(kBlock, 3) k_render_bwd(const RenderArgs A)
                     hit = evaluate(slot_at(w, b), get_pix(w, l), A.sigma, A.alpha_min,
                                    A.alpha_max, h);
                 }
-                // each pixel lane walks its hits of the round back to front: transmittance,
-                // suffix sums, and dL/dalpha_k with the weight handed back to the hit's lane
+                // the pixel's channel gradients meet the hit's channels in its own lane:
+                // X_k = sum_ch g_ch x_ch,k (x = d, 1, n)
+                const float gDl = __shfl_sync(kFull, gD, l);
+                const float gOl = __shfl_sync(kFull, gO, l);
+                const float gNl0 = __shfl_sync(kFull, gN0, l);
+                const float gNl1 = __shfl_sync(kFull, gN1, l);
+                const float gNl2 = __shfl_sync(kFull, gN2, l);
+                float X = 0.0f, inv_om = 0.0f;
+                if (hit) {
+                    const float4 nn = w.n[b];
+                    X = gDl * h.d + gOl + gNl0 * nn.x + gNl1 * nn.y + gNl2 * nn.z;
+                    inv_om = __fdividef(1.0f, __fsub_rn(1.0f, h.a));
+                }
+                // each pixel lane walks its hits of the round back to front: T_k = T_{k+1} /
+                // (1 - alpha_k) and dL/dalpha_k = T_k X_k - Y / (1 - alpha_k), with
+                // Y = sum_ch g_ch B_ch,k kept as one suffix sum (Y += w_k X_k), handing
+                // dL/dalpha_k and the weight back to the hit's lane
                 uint32_t mine = lanes_keyed_to_me(hit, l, lane);
                 while (__any_sync(kFull, mine != 0u)) {
                     const bool have = mine != 0u;
                     const int src = have ? __ffs(mine) - 1 : lane;
                     mine &= mine - 1u;
                     const float a = __shfl_sync(kFull, h.a, src);
-                    const float d = __shfl_sync(kFull, h.d, src);
-                    const int bc = __shfl_sync(kFull, b | (h.clamped ? 0x100 : 0), src);
+                    const float xk = __shfl_sync(kFull, X, src);
+                    const float io = __shfl_sync(kFull, inv_om, src);
                     if (have) {
-                        const float inv_om = __fdividef(1.0f, __fsub_rn(1.0f, a));
-                        const float Tk = T * inv_om;
+                        const float Tk = T * io;
                         const float wgt = __fmul_rn(a, Tk);
-                        const float4 nn = w.n[bc & 0xFF];
-                        // dL/dalpha_k = sum_ch g_ch (x_k A_k - B_ch,k / (1 - alpha_k))
-                        float gA = gD * (d * Tk - Bd * inv_om);
-                        gA += gO * (Tk - Bo * inv_om);
-                        gA += gN0 * (nn.x * Tk - Bn0 * inv_om);
-                        gA += gN1 * (nn.y * Tk - Bn1 * inv_om);
-                        gA += gN2 * (nn.z * Tk - Bn2 * inv_om);
-                        Bd += wgt * d;
-                        Bo += wgt;
-                        Bn0 += wgt * nn.x;
-                        Bn1 += wgt * nn.y;
-                        Bn2 += wgt * nn.z;
+                        const float gA = Tk * xk - Y * io;
+                        Y += wgt * xk;
                         T = Tk;
-                        gwl[src] = make_float2((bc & 0x100) ? 0.0f : gA, wgt);
+                        gwl[src] = make_float2(gA, wgt);
                     }
                 }
-                const float gDl = __shfl_sync(kFull, gD, l);
-                const float gNl0 = __shfl_sync(kFull, gN0, l);
-                const float gNl1 = __shfl_sync(kFull, gN1, l);
-                const float gNl2 = __shfl_sync(kFull, gN2, l);
                 __syncwarp();
                 float g[16];
 #pragma unroll
                 for (int c = 0; c < 16; ++c) g[c] = 0.0f;
                 if (hit) {
                     const float2 gw = gwl[lane];
-                    const float gAe = gw.x, wgt = gw.y;
+                    const float gAe = h.clamped ? 0.0f : gw.x, wgt = gw.y;
                     const SlotRef st = slot_at(w, b);
                     const Pix px = get_pix(w, l);
                     const float gd = gDl * wgt;            // dL/dd_k
@@ -752,7 +783,8 @@ __global__ void __launch_bounds__(kBlock, 3) k_render_bwd(const RenderArgs A)
                 }
                 // sum the group's four lanes (one primitive) by recursive halving: after the
                 // exchange across lane bit 0 a lane keeps 8 of the 16 values, after bit 1 it
-                // keeps 4; groups of one primitive in the same round meet in the atomics
+                // keeps 4 (indices base .. base + 3); then add up the groups of one primitive
+                // (consecutive groups) towards its first group of the round, which alone writes
                 const uint32_t hm = __ballot_sync(kFull, hit);
                 if (hm != 0u) {
 #pragma unroll
@@ -769,11 +801,23 @@ __global__ void __launch_bounds__(kBlock, 3) k_render_bwd(const RenderArgs A)
                         const float keep = up ? g[c + 4] : g[c];
                         g[c] = keep + __shfl_xor_sync(kFull, send, 2);
                     }
-                    if ((hm >> (lane & ~3)) & 0xFu) {
+#pragma unroll
+                    for (int s = 4; s < 32; s <<= 1) {
+                        const int bo = __shfl_down_sync(kFull, b, s);
+                        const bool same = lane + s < 32 && bo == b;
+#pragma unroll
+                        for (int c = 0; c < 4; ++c) {
+                            const float o = __shfl_down_sync(kFull, g[c], s);
+                            g[c] += same ? o : 0.0f;
+                        }
+                    }
+                    const int bp4 = __shfl_up_sync(kFull, b, 4);
+                    const bool first = lane < 4 || bp4 != b;
+                    if (first && ((hm >> (lane & ~3)) != 0u)) {
                         const int base = ((lane & 1) ? 8 : 0) + ((lane & 2) ? 4 : 0);
 #pragma unroll
                         for (int c = 0; c < 4; ++c)
-                            if (base + c < kAcc) atomicAdd(&acc[b][base + c], g[c]);
+                            if (base + c < kAcc) acc[b][base + c] += g[c];
                     }
                 }
                 __syncwarp();
