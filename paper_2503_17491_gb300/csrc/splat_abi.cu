@@ -107,6 +107,7 @@ struct splat_ctx {
     bool rendered = false;
     int64_t last_n = 0;
     uint32_t *sorted_keys = nullptr, *sorted_vals = nullptr;
+    uint32_t *entry_rect = nullptr;   // per list entry: rectangle inside its tile (K4)
 };
 
 namespace {
@@ -140,7 +141,7 @@ splat::RenderArgs render_args(splat_ctx *ctx, const splat_gaussians *g)
     a.ranges = ctx->d_ranges;
     a.tile_order = ctx->d_tile_order;
     a.sorted_vals = ctx->sorted_vals;
-    a.recs = ctx->d_recs;
+    a.entry_rect = ctx->entry_rect;
     a.n_tiles = ctx->n_tiles;
     a.n_items = ctx->n_tiles * (splat::kBlock / 32);
     a.alpha_min = ctx->cfg.alpha_min;
@@ -180,10 +181,14 @@ int render_core(splat_ctx *ctx, const splat_gaussians *g, float *depth, float *n
     CK(splat::radix_sort_pairs(ctx->d_tkeys, ctx->d_tvals, ctx->d_tkeys2, ctx->d_tvals2, cnt,
                                ctx->cap.max_pairs, bits_for(ctx->n_tiles), ctx->d_hist, &tk, &tv,
                                st));
-    CK(splat::launch_ranges(tk, cnt, ctx->cap.max_pairs, ctx->d_ranges, ctx->n_tiles, st));
+    // the tile sort's other value buffer is free: it takes the entries' tile rectangles
+    uint32_t *rects = tv == ctx->d_tvals ? ctx->d_tvals2 : ctx->d_tvals;
+    CK(splat::launch_ranges(tk, tv, ctx->d_recs, ctx->d_tileinfo, th, tw, cnt,
+                            ctx->cap.max_pairs, ctx->d_ranges, ctx->n_tiles, rects, st));
     CK(splat::launch_order_tiles(ctx->d_ranges, ctx->n_tiles, ctx->d_tile_order, st));
     ctx->sorted_keys = tk;
     ctx->sorted_vals = tv;
+    ctx->entry_rect = rects;
     splat::RenderArgs a = render_args(ctx, g);
     a.depth = depth;
     a.normal = normal;

@@ -228,8 +228,57 @@ cudaError_t launch_emit(const uint32_t *sorted_pair_ids, int64_t n_pairs_total, 
                         uint32_t *block_sums, uint32_t *tile_keys, uint32_t *tile_vals,
                         int64_t max_pairs, uint32_t *d_count, uint32_t *status, cudaStream_t st);
 
-cudaError_t launch_ranges(const uint32_t *tile_keys, const uint32_t *d_count, int64_t max_pairs,
-                          uint2 *ranges, int64_t n_tiles, cudaStream_t st);
+// Pixel rectangle of a (view, primitive) record inside tile (tr, tc) of a tile_h x tile_w
+// tiling, packed as 4 bytes (r_lo, r_hi, c_lo, c_hi) with the record's normal-flip bit in bit 31;
+// the record's columns are cyclic modulo the image width cols.  0xFF (r_lo > r_hi) when empty.
+constexpr uint32_t kRectFlip = 0x80000000u;
+
+__device__ __forceinline__ uint32_t tile_local_rect(const PairRec &rec, int tr, int tc, int cols,
+                                                    int tile_h, int tile_w)
+{
+    const int rb = tr * tile_h, cb = tc * tile_w;
+    int r_lo = rec.r0 - rb, r_hi = rec.r1 - rb;
+    r_lo = r_lo < 0 ? 0 : r_lo;
+    r_hi = r_hi > tile_h - 1 ? tile_h - 1 : r_hi;
+    if (r_lo > r_hi) return 0xFFu;
+    const int W = cols, nc = rec.nc;
+    int c_lo, c_hi;
+    if (nc >= W) {
+        c_lo = 0;
+        c_hi = tile_w - 1;
+    } else {
+        int d = cb - rec.c0;     // tile start relative to the range start, in [0, W)
+        d += d < 0 ? W : 0;
+        int e = rec.c0 - cb;     // range start relative to the tile start, in [0, W)
+        e += e < 0 ? W : 0;
+        const bool start_in = d < nc;
+        const bool begins_here = e < tile_w;
+        if (start_in && begins_here && d != 0) {   // both ends of a wrapping range meet here
+            c_lo = 0;
+            c_hi = tile_w - 1;
+        } else if (start_in) {
+            c_lo = 0;
+            c_hi = nc - 1 - d;
+            c_hi = c_hi > tile_w - 1 ? tile_w - 1 : c_hi;
+        } else if (begins_here) {
+            c_lo = e;
+            c_hi = e + nc - 1;
+            c_hi = c_hi > tile_w - 1 ? tile_w - 1 : c_hi;
+        } else {
+            return 0xFFu;
+        }
+    }
+    return static_cast<uint32_t>(r_lo) | (static_cast<uint32_t>(r_hi) << 8) |
+           (static_cast<uint32_t>(c_lo) << 16) | (static_cast<uint32_t>(c_hi) << 24) |
+           ((rec.cf & kPairFlip) ? kRectFlip : 0u);
+}
+
+// K4: [start, end) per tile from the sorted tile ids, and every list entry's pixel rectangle
+// inside its tile (tile_local_rect) in entry_rect
+cudaError_t launch_ranges(const uint32_t *tile_keys, const uint32_t *tile_vals,
+                          const PairRec *recs, const TileInfo *tiles, int tile_h, int tile_w,
+                          const uint32_t *d_count, int64_t max_pairs, uint2 *ranges,
+                          int64_t n_tiles, uint32_t *entry_rect, cudaStream_t st);
 
 // tiles ordered by decreasing log2 of their list length (order inside a bucket unspecified)
 cudaError_t launch_order_tiles(const uint2 *ranges, int64_t n_tiles, uint32_t *order,
@@ -245,7 +294,7 @@ struct RenderArgs {
     const uint2 *ranges;          // global tile -> [start, end)
     const uint32_t *tile_order;   // tiles in decreasing order of list length (work order)
     const uint32_t *sorted_vals;  // pair ids in (tile, range, id) order
-    const PairRec *recs;
+    const uint32_t *entry_rect;   // per list entry: pixel rectangle inside its tile, flip bit
     int64_t n_tiles;
     int64_t n_items;              // n_tiles x blocks per tile
     float alpha_min, alpha_max, t_min, sigma;

@@ -279,7 +279,9 @@ extern "C" SPLAT_API int splat_render_noalloc(const splat_gaussians *g,
     uint32_t *tk, *tv;
     NA_CK(splat::radix_sort_pairs(tkeys, tvals, tkeys2, tvals2, cnt, kMaxPairs, bits_for(n_tiles),
                                   hist, &tk, &tv, st));
-    NA_CK(splat::launch_ranges(tk, cnt, kMaxPairs, ranges, n_tiles, st));
+    uint32_t *rects = tv == tvals ? tvals2 : tvals;   // the tile sort's free value buffer
+    NA_CK(splat::launch_ranges(tk, tv, recs, tiles, th, tw, cnt, kMaxPairs, ranges, n_tiles, rects,
+                               st));
     NA_CK(splat::launch_order_tiles(ranges, n_tiles, order, st));
 
     splat::RenderArgs a{};
@@ -292,7 +294,7 @@ extern "C" SPLAT_API int splat_render_noalloc(const splat_gaussians *g,
     a.ranges = ranges;
     a.tile_order = order;
     a.sorted_vals = tv;
-    a.recs = recs;
+    a.entry_rect = rects;
     a.n_tiles = n_tiles;
     a.n_items = n_tiles * (splat::kBlock / 32);
     a.alpha_min = cfg.alpha_min;

@@ -116,47 +116,6 @@ __device__ __forceinline__ Pix load_pix(const PixFrame *table, int index)
     return p;
 }
 
-// pixel rectangle of a primitive inside the tile, packed as 4 bytes (r_lo, r_hi, c_lo, c_hi);
-// the record's columns are cyclic modulo the image width
-template <int TH, int TW>
-__device__ __forceinline__ uint32_t local_rect(const PairRec &rec, const TileInfo &ti)
-{
-    const int rb = ti.tr * TH, cb = ti.tc * TW;
-    int r_lo = rec.r0 - rb, r_hi = rec.r1 - rb;
-    r_lo = r_lo < 0 ? 0 : r_lo;
-    r_hi = r_hi > TH - 1 ? TH - 1 : r_hi;
-    if (r_lo > r_hi) return 0xFFu;   // empty: r_lo = 255 > r_hi = 0
-    const int W = ti.cols, nc = rec.nc;
-    int c_lo, c_hi;
-    if (nc >= W) {
-        c_lo = 0;
-        c_hi = TW - 1;
-    } else {
-        int d = cb - rec.c0;     // tile start relative to the range start, in [0, W)
-        d += d < 0 ? W : 0;
-        int e = rec.c0 - cb;     // range start relative to the tile start, in [0, W)
-        e += e < 0 ? W : 0;
-        const bool start_in = d < nc;
-        const bool begins_here = e < TW;
-        if (start_in && begins_here && d != 0) {   // both ends of a wrapping range meet here
-            c_lo = 0;
-            c_hi = TW - 1;
-        } else if (start_in) {
-            c_lo = 0;
-            c_hi = nc - 1 - d;
-            c_hi = c_hi > TW - 1 ? TW - 1 : c_hi;
-        } else if (begins_here) {
-            c_lo = e;
-            c_hi = e + nc - 1;
-            c_hi = c_hi > TW - 1 ? TW - 1 : c_hi;
-        } else {
-            return 0xFFu;
-        }
-    }
-    return static_cast<uint32_t>(r_lo) | (static_cast<uint32_t>(r_hi) << 8) |
-           (static_cast<uint32_t>(c_lo) << 16) | (static_cast<uint32_t>(c_hi) << 24);
-}
-
 // pixel mask of a rectangle over the 4 x 8 block with top-left (br, bc): bit 8 r + c for the
 // block's row r and column c
 __device__ __forceinline__ uint32_t pixel_mask(uint32_t rect, int br, int bc)
@@ -424,16 +383,16 @@ __device__ __forceinline__ BlockPix block_pixel(const TileInfo &ti, int blk, int
     return b;
 }
 
-// read one list entry per lane: pair id, rectangle, whether it meets the block
+// read one list entry per lane: pair id, rectangle inside the tile, whether it meets the block
 template <int TH, int TW>
 __device__ __forceinline__ bool read_entry(const RenderArgs &A, const TileInfo &ti, uint32_t j,
                                            const BlockPix &bp, uint32_t &p, uint32_t &rect,
                                            bool &flip)
 {
     p = A.sorted_vals[j];
-    const PairRec rec = A.recs[p];
-    rect = local_rect<TH, TW>(rec, ti);
-    flip = (rec.cf & kPairFlip) != 0;
+    const uint32_t r = A.entry_rect[j];
+    flip = (r & kRectFlip) != 0u;
+    rect = r & ~kRectFlip;
     return pixel_mask(rect, bp.br, bp.bc) != 0u;
 }
 

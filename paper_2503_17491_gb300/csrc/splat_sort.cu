@@ -286,9 +286,13 @@ __global__ void __launch_bounds__(kThreads) k_emit(
     }
 }
 
-// K4: [start, end) per tile from sorted tile ids (ranges zeroed before)
-__global__ void k_ranges(const uint32_t *__restrict__ keys, const uint32_t *d_count,
-                         int64_t max_pairs, uint2 *__restrict__ ranges)
+// K4: [start, end) per tile from sorted tile ids (ranges zeroed before), and each entry's pixel
+// rectangle inside its tile, so that the renderer's warps (eight per tile) need not each gather
+// the record and clip it
+__global__ void k_ranges(const uint32_t *__restrict__ keys, const uint32_t *__restrict__ vals,
+                         const PairRec *__restrict__ recs, const TileInfo *__restrict__ tiles,
+                         int tile_h, int tile_w, const uint32_t *d_count, int64_t max_pairs,
+                         uint2 *__restrict__ ranges, uint32_t *__restrict__ entry_rect)
 {
     const int64_t m = clamp_count(d_count, max_pairs);
     for (int64_t j = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; j < m;
@@ -296,6 +300,8 @@ __global__ void k_ranges(const uint32_t *__restrict__ keys, const uint32_t *d_co
         const uint32_t t = keys[j];
         if (j == 0 || keys[j - 1] != t) ranges[t].x = static_cast<uint32_t>(j);
         if (j == m - 1 || keys[j + 1] != t) ranges[t].y = static_cast<uint32_t>(j + 1);
+        const TileInfo &ti = tiles[t];
+        entry_rect[j] = tile_local_rect(recs[vals[j]], ti.tr, ti.tc, ti.cols, tile_h, tile_w);
     }
 }
 
@@ -377,12 +383,15 @@ cudaError_t launch_emit(const uint32_t *sorted_pair_ids, int64_t n_pairs_total, 
     return cudaGetLastError();
 }
 
-cudaError_t launch_ranges(const uint32_t *tile_keys, const uint32_t *d_count, int64_t max_pairs,
-                          uint2 *ranges, int64_t n_tiles, cudaStream_t st)
+cudaError_t launch_ranges(const uint32_t *tile_keys, const uint32_t *tile_vals,
+                          const PairRec *recs, const TileInfo *tiles, int tile_h, int tile_w,
+                          const uint32_t *d_count, int64_t max_pairs, uint2 *ranges,
+                          int64_t n_tiles, uint32_t *entry_rect, cudaStream_t st)
 {
     cudaError_t e = cudaMemsetAsync(ranges, 0, sizeof(uint2) * static_cast<size_t>(n_tiles), st);
     if (e != cudaSuccess) return e;
-    k_ranges<<<4 * kSortGrid, 256, 0, st>>>(tile_keys, d_count, max_pairs, ranges);
+    k_ranges<<<4 * kSortGrid, 256, 0, st>>>(tile_keys, tile_vals, recs, tiles, tile_h, tile_w,
+                                            d_count, max_pairs, ranges, entry_rect);
     return cudaGetLastError();
 }
 
