@@ -26,9 +26,10 @@
 // frame Q = (e1, e2, e3) -- e1 the ray through the tile centre, e2 and e3 its two planes -- and
 // a primitive is staged as Q b, with the centre Q b_c kept as a float pair; Q R^c_w, Q t^c_w and
 // the pixel planes in that frame come from tables computed in FP64 on the host (float pairs).
-// A pair first takes the binary32 box test with a 1% margin; only pairs that pass recompute
-// h_x.b_c and h_y.b_c in float-pair arithmetic (two-product / two-sum) and take the exact test,
-// so the costly path runs on hits only and grazing rays keep their accuracy.
+// h_x.b_c and h_y.b_c are formed in float-pair arithmetic (two-product / two-sum), so grazing
+// rays at range keep their accuracy.  (A cheaper binary32 pre-test that skipped this for clear
+// misses paid off only while all lanes of a warp evaluated one primitive: with 32 different pairs
+// per warp some lane always passes it.)
 //
 // The range is d = nu . v (nu lies on the ray, so this equals |nu| without a square root) and
 // a hit counts only when d > 0 (in front of the sensor).  Cutoffs: alpha clamped at alpha_max,
@@ -54,7 +55,6 @@
 namespace splat {
 namespace {
 
-constexpr float kLooseBox = 1.01f;   // margin of the binary32 pre-test
 constexpr int kWarps = kBlock / 32;  // warps per CTA (independent)
 constexpr int kBlocksPerTile = kBlock / 32;
 constexpr int kAcc = 13;             // per staged primitive: g_ba'(3) g_bb'(3) g_c'(3) g_n(3) g_o
@@ -302,23 +302,17 @@ __device__ __forceinline__ bool evaluate(const SlotRef &s, const Pix &px, float 
 {
     h.ha0 = dot3e(px.hx0, px.hx1, px.hx2, s.a.x, s.a.y, s.a.z);
     h.ha1 = dot3e(px.hx0, px.hx1, px.hx2, s.b.x, s.b.y, s.b.z);
-    h.ha2 = dot3e(px.hx0, px.hx1, px.hx2, s.c.x, s.c.y, s.c.z);
     h.hb0 = dot3e(px.hy0, px.hy1, px.hy2, s.a.x, s.a.y, s.a.z);
     h.hb1 = dot3e(px.hy0, px.hy1, px.hy2, s.b.x, s.b.y, s.b.z);
-    h.hb2 = dot3e(px.hy0, px.hy1, px.hy2, s.c.x, s.c.y, s.c.z);
-    h.pz = __fmaf_rn(h.ha0, h.hb1, -__fmul_rn(h.ha1, h.hb0));
-    const float pxx = __fmaf_rn(h.ha1, h.hb2, -__fmul_rn(h.ha2, h.hb1));
-    const float pyy = __fmaf_rn(h.ha2, h.hb0, -__fmul_rn(h.ha0, h.hb2));
-    const float apz = fabsf(h.pz);
-    if (!(apz > 0.0f) ||
-        !(fmaxf(fabsf(pxx), fabsf(pyy)) <= __fmul_rn(sigma * kLooseBox, apz)))
-        return false;
-    // precise lateral offsets of the centre from the two pixel planes
+    // lateral offsets of the centre from the two pixel planes, in float-pair arithmetic
     h.ha2 = dot3_f2(px.hx0, px.hx1, px.hx2, px.hxl0, px.hxl1, s.c, s.c.w, s.n.w);
     h.hb2 = dot3_f2(px.hy0, px.hy1, px.hy2, px.hyl0, px.hyl1, s.c, s.c.w, s.n.w);
+    h.pz = __fmaf_rn(h.ha0, h.hb1, -__fmul_rn(h.ha1, h.hb0));
     h.px = __fmaf_rn(h.ha1, h.hb2, -__fmul_rn(h.ha2, h.hb1));
     h.py = __fmaf_rn(h.ha2, h.hb0, -__fmul_rn(h.ha0, h.hb2));
-    if (!(fmaxf(fabsf(h.px), fabsf(h.py)) <= __fmul_rn(sigma, apz))) return false;
+    const float apz = fabsf(h.pz);
+    if (!(apz > 0.0f) || !(fmaxf(fabsf(h.px), fabsf(h.py)) <= __fmul_rn(sigma, apz)))
+        return false;
     h.inv = __fdividef(1.0f, h.pz);
     h.sa = __fmul_rn(h.px, h.inv);
     h.sb = __fmul_rn(h.py, h.inv);
