@@ -58,7 +58,7 @@
 
 #define OR_PI 3.14159265358979323846
 
-int or_version(void) { return 5; }
+int or_version(void) { return 6; }
 
 /* ------------------------------------------------------------------------- */
 /* 1. pose                                                                   */
@@ -222,6 +222,18 @@ float or_contract_logf(float x)
  * Out: pixel rows [r0, r1], cyclic pixel columns [c0, c0 + nc) mod W, tile rows [tr0, tr1],
  * cyclic tile columns [tc0, tc0 + ntc) mod TC.  Returns the number of tiles (0 when no pixel ray
  * can reach the region). */
+/* keep the higher and the lower of the points seen so far, by elevation atan2(z, r), r >= 0:
+ * z r' > z' r says that (z, r) lies above (z', r'); the first of equal points stays */
+static void elev_candidate(float z, float r, float *zh, float *rh, float *zl, float *rl, int *have)
+{
+    if (!*have) {
+        *zh = z; *rh = r; *zl = z; *rl = r; *have = 1;
+        return;
+    }
+    if (z * *rh > *zh * r) { *zh = z; *rh = r; }
+    if (z * *rl < *zl * r) { *zl = z; *rl = r; }
+}
+
 static int contract_bbox(f3 ba, f3 bb, f3 bc, float o, float alpha_min, float sigma, int H,
                          int W, float emin, float emax, int th, int tw, int32_t *pix,
                          int32_t *til)
@@ -281,12 +293,14 @@ static int contract_bbox(f3 ba, f3 bb, f3 bc, float o, float alpha_min, float si
         }
     }
 
-    float th_lo = INFINITY, th_hi = -INFINITY;
+    /* elevation: the highest and the lowest of the vertices and of the edges' interior extrema,
+     * ordered by z / |xy| without a division (z_i r_j against z_j r_i); one arctangent each */
+    float zh = 0.0f, rh = 0.0f, zl = 0.0f, rl = 0.0f;
+    int have = 0;
     for (int i = 0; i < nv; ++i) {
         f3 p = P[i], q = P[(i + 1) % nv];
         float rxy = sqrtf(p.x * p.x + p.y * p.y);
-        float e = or_contract_atan2f(p.z, rxy);
-        th_lo = fminf(th_lo, e); th_hi = fmaxf(th_hi, e);
+        elev_candidate(p.z, rxy, &zh, &rh, &zl, &rl, &have);
         f3 d = { q.x - p.x, q.y - p.y, q.z - p.z };
         float pd = p.x * d.x + p.y * d.y;
         float pp = p.x * p.x + p.y * p.y;
@@ -297,11 +311,11 @@ static int contract_bbox(f3 ba, f3 bb, f3 bc, float o, float alpha_min, float si
             float lam = num / den;
             if (lam > 0.0f && lam < 1.0f) {
                 f3 X = { p.x + lam * d.x, p.y + lam * d.y, p.z + lam * d.z };
-                float e2 = or_contract_atan2f(X.z, sqrtf(X.x * X.x + X.y * X.y));
-                th_lo = fminf(th_lo, e2); th_hi = fmaxf(th_hi, e2);
+                elev_candidate(X.z, sqrtf(X.x * X.x + X.y * X.y), &zh, &rh, &zl, &rl, &have);
             }
         }
     }
+    float th_hi = or_contract_atan2f(zh, rh), th_lo = or_contract_atan2f(zl, rl);
     if (pole_n) th_hi = C_HALF_PI;
     if (pole_s) th_lo = -C_HALF_PI;
 
@@ -317,14 +331,19 @@ static int contract_bbox(f3 ba, f3 bb, f3 bc, float o, float alpha_min, float si
     if (inside) {
         c0 = 0; nc = W;
     } else {
+        /* the polygon's xy-shadow misses the origin, so it spans less than pi in azimuth: the
+         * extreme vertices follow from the signs of cross products, one arctangent each,
+         * relative to the centre direction */
         float gc = or_contract_atan2f(C.y, C.x);
-        float dmin = INFINITY, dmax = -INFINITY;
-        for (int i = 0; i < nv; ++i) {
-            float cr = C.x * P[i].y - C.y * P[i].x;
-            float dt = C.x * P[i].x + C.y * P[i].y;
-            float dl = or_contract_atan2f(cr, dt);
-            dmin = fminf(dmin, dl); dmax = fmaxf(dmax, dl);
+        int imin = 0, imax = 0;
+        for (int i = 1; i < nv; ++i) {
+            if (P[imax].x * P[i].y - P[imax].y * P[i].x > 0.0f) imax = i;
+            if (P[imin].x * P[i].y - P[imin].y * P[i].x < 0.0f) imin = i;
         }
+        float dmax = or_contract_atan2f(C.x * P[imax].y - C.y * P[imax].x,
+                                        C.x * P[imax].x + C.y * P[imax].y);
+        float dmin = or_contract_atan2f(C.x * P[imin].y - C.y * P[imin].x,
+                                        C.x * P[imin].x + C.y * P[imin].y);
         float glo = gc + dmin, ghi = gc + dmax;
         float kc = (float)W / C_TWO_PI;
         float uf = ((C_PI - ghi) * kc - 0.5f) - eps;

@@ -114,14 +114,28 @@ __device__ __forceinline__ v3 rot(const float *R, v3 v)
               (R[6] * v.x + R[7] * v.y) + R[8] * v.z};
 }
 
+// keep the higher and the lower of the points seen so far, by elevation atan2(z, r), r >= 0:
+// z r' > z' r says that (z, r) lies above (z', r'); the first of equal points stays
+__device__ __forceinline__ void elev_candidate(float z, float r, float &zh, float &rh, float &zl,
+                                               float &rl, bool &have)
+{
+    if (!have) {
+        zh = z; rh = r; zl = z; rl = r;
+        have = true;
+        return;
+    }
+    if (z * rh > zh * r) { zh = z; rh = r; }
+    if (z * rl < zl * r) { zl = z; rl = r; }
+}
+
 // Spherical bounding box of the splat-space region where the primitive can contribute: the
 // 3-sigma box |s|_inf <= sigma intersected with the disk where o G(s) >= alpha_min, i.e.
 // |s| <= r_o = sqrt(2 ln(o / alpha_min)), bounded by |s|_inf <= a = min(sigma, r_o) and the
 // diamond |s_a| + |s_b| <= sqrt2 r_o (an octagon when it cuts the corners), r_o widened by
 // 0.1 % + 0.002.  The polygon maps to P = b_c + s_a b_alpha + s_b b_beta.  Azimuth: every column
-// when the z axis pierces the polygon's xy-shadow, else the vertex azimuths relative to the
-// centre direction.  Elevation: vertices, each edge's interior extremum (where z / |xy| is
-// stationary along the edge), and the pole the z axis reaches.  Returns the tile count and
+// when the z axis pierces the polygon's xy-shadow, else the extreme vertex azimuths relative to
+// the centre direction.  Elevation: the extreme of the vertices and each edge's interior extremum
+// (where z / |xy| is stationary along the edge), and the pole the z axis reaches.  Returns the tile count and
 // fills the record's pixel rectangle.
 __device__ uint32_t contract_bbox(v3 ba, v3 bb, v3 bc, float o, float alpha_min, float sigma,
                                   const ViewDesc &vd, int tile_h, int tile_w, PairRec &rec)
@@ -187,12 +201,13 @@ __device__ uint32_t contract_bbox(v3 ba, v3 bb, v3 bc, float o, float alpha_min,
         }
     }
 
-    float el_lo = INFINITY, el_hi = -INFINITY;
+    // elevation: the highest and the lowest of the vertices and of the edges' interior extrema,
+    // ordered by z / |xy| without a division (z_i r_j against z_j r_i); one arctangent each
+    float zh = 0.0f, rh = 0.0f, zl = 0.0f, rl = 0.0f;
+    bool have = false;
     for (int i = 0; i < nv; ++i) {
         const v3 p = P[i], q = P[(i + 1) % nv];
-        const float e = contract_atan2(p.z, sqrtf(p.x * p.x + p.y * p.y));
-        el_lo = fminf(el_lo, e);
-        el_hi = fmaxf(el_hi, e);
+        elev_candidate(p.z, sqrtf(p.x * p.x + p.y * p.y), zh, rh, zl, rl, have);
         const v3 d{q.x - p.x, q.y - p.y, q.z - p.z};
         const float pd = p.x * d.x + p.y * d.y;
         const float pp = p.x * p.x + p.y * p.y;
@@ -203,12 +218,11 @@ __device__ uint32_t contract_bbox(v3 ba, v3 bb, v3 bc, float o, float alpha_min,
             const float lam = num / den;
             if (lam > 0.0f && lam < 1.0f) {
                 const v3 X{p.x + lam * d.x, p.y + lam * d.y, p.z + lam * d.z};
-                const float e2 = contract_atan2(X.z, sqrtf(X.x * X.x + X.y * X.y));
-                el_lo = fminf(el_lo, e2);
-                el_hi = fmaxf(el_hi, e2);
+                elev_candidate(X.z, sqrtf(X.x * X.x + X.y * X.y), zh, rh, zl, rl, have);
             }
         }
     }
+    float el_hi = contract_atan2(zh, rh), el_lo = contract_atan2(zl, rl);
     if (north) el_hi = kHalfPi;
     if (south) el_lo = -kHalfPi;
 
@@ -226,15 +240,19 @@ __device__ uint32_t contract_bbox(v3 ba, v3 bb, v3 bc, float o, float alpha_min,
         c0 = 0;
         nc = W;
     } else {
+        // the polygon's xy-shadow misses the origin, so it spans less than pi in azimuth: the
+        // extreme vertices follow from the signs of cross products, one arctangent each,
+        // relative to the centre direction
         const float gc = contract_atan2(C.y, C.x);
-        float dmin = INFINITY, dmax = -INFINITY;
-        for (int i = 0; i < nv; ++i) {
-            const float cr = C.x * P[i].y - C.y * P[i].x;
-            const float dt = C.x * P[i].x + C.y * P[i].y;
-            const float dl = contract_atan2(cr, dt);
-            dmin = fminf(dmin, dl);
-            dmax = fmaxf(dmax, dl);
+        int imin = 0, imax = 0;
+        for (int i = 1; i < nv; ++i) {
+            if (P[imax].x * P[i].y - P[imax].y * P[i].x > 0.0f) imax = i;
+            if (P[imin].x * P[i].y - P[imin].y * P[i].x < 0.0f) imin = i;
         }
+        const float dmax = contract_atan2(C.x * P[imax].y - C.y * P[imax].x,
+                                          C.x * P[imax].x + C.y * P[imax].y);
+        const float dmin = contract_atan2(C.x * P[imin].y - C.y * P[imin].x,
+                                          C.x * P[imin].x + C.y * P[imin].y);
         const float glo = gc + dmin, ghi = gc + dmax;
         const float kc = static_cast<float>(W) / kTwoPi;
         const float uf = ((kPi - ghi) * kc - 0.5f) - kPixelMargin;
