@@ -13,7 +13,8 @@
 // The sort is a reduce-then-scan LSD radix sort with 8-bit digits on a fixed grid of CTAs, so
 // that the element count can live on the device (it is data dependent after emission) and the
 // whole pipeline can be captured in a CUDA graph.  Ranking inside a CTA tile is warp-level
-// (match.any) and stable in (warp, item, lane) = index order.
+// (match.any) and stable in (warp, item, lane) = index order; the ranked tile is first sorted
+// by digit in shared memory and then written out run by run, so that global stores coalesce.
 
 #include "splat_internal.cuh"
 
@@ -92,6 +93,9 @@ __global__ void __launch_bounds__(kThreads) k_downsweep(
     __shared__ uint32_t s_base[kRadix];          // running global offset per digit
     __shared__ uint32_t s_wcnt[kWarps][kRadix];  // per-warp digit counts -> warp prefixes
     __shared__ uint32_t s_tile[kRadix];          // digit totals of the current tile
+    __shared__ uint32_t s_toff[kRadix];          // digit offsets inside the current tile
+    __shared__ uint32_t s_wsum[kWarps];
+    __shared__ uint32_t s_key[kSortTile], s_val[kSortTile];   // the tile, sorted by digit
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int64_t n = clamp_count(d_count, max_n);
     const int64_t chunk = chunk_of(n, gridDim.x);
@@ -146,15 +150,39 @@ __global__ void __launch_bounds__(kThreads) k_downsweep(
                 run += c;
             }
             s_tile[tid] = run;
+            // the digit's offset inside the tile: exclusive scan of the tile totals over digits
+            uint32_t x = run;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, x, o);
+                if (lane >= o) x += y;
+            }
+            if (lane == 31) s_wsum[warp] = x;
+            __syncthreads();
+            uint32_t wbase = 0;
+            for (int w = 0; w < warp; ++w) wbase += s_wsum[w];
+            s_toff[tid] = wbase + x - run;
         }
         __syncthreads();
+        // sort the tile by digit in shared memory (stable: warp, item, lane order) ...
 #pragma unroll
         for (int it = 0; it < kItems; ++it) {
             if (dig[it] < kRadix) {
-                const uint32_t pos = s_base[dig[it]] + s_wcnt[warp][dig[it]] + rank[it];
-                keys_out[pos] = key[it];
-                vals_out[pos] = val[it];
+                const uint32_t lpos = s_toff[dig[it]] + s_wcnt[warp][dig[it]] + rank[it];
+                s_key[lpos] = key[it];
+                s_val[lpos] = val[it];
             }
+        }
+        __syncthreads();
+        // ... and write each digit's run to its global place: consecutive threads, consecutive
+        // addresses
+        const int cnt = static_cast<int>(end - tb < kSortTile ? end - tb : kSortTile);
+        for (int i = tid; i < cnt; i += kThreads) {
+            const uint32_t k = s_key[i];
+            const int d = static_cast<int>((k >> shift) & 0xFF);
+            const uint32_t pos = s_base[d] + (static_cast<uint32_t>(i) - s_toff[d]);
+            keys_out[pos] = k;
+            vals_out[pos] = s_val[i];
         }
         __syncthreads();
         s_base[tid] += s_tile[tid];
