@@ -18,6 +18,7 @@ import argparse
 import json
 import math
 import os
+import re
 import statistics
 import subprocess
 import sys
@@ -169,6 +170,38 @@ def build_workload(index, n=None, keyframes=None):
     if n or keyframes:
         desc += f" [reduced: {s.n} primitives, {len(views)} keyframes]"
     return s, views, targets, desc
+
+
+TRAFFIC_MD = os.path.join(ROOT, "profiles", "render_dram_traffic_12kf_500k.md")
+
+
+def csrc_digest():
+    """sha256 over the library's CUDA sources (names and contents, in name order), 16 hex digits."""
+    import glob
+    import hashlib
+    h = hashlib.sha256()
+    d = os.path.join(ROOT, "paper_2503_17491_gb300", "csrc")
+    files = glob.glob(os.path.join(d, "*.cu")) + glob.glob(os.path.join(d, "*.cuh"))
+    for f in sorted(files, key=os.path.basename):
+        h.update(os.path.basename(f).encode())
+        with open(f, "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(kernel, tile):
+    """DRAM read+write bytes per launch of `kernel` at `tile`, from the committed ncu summary of
+    the full workload -- only while the library sources are the ones it was captured from."""
+    try:
+        with open(TRAFFIC_MD) as f:
+            text = f.read()
+    except OSError:
+        return None
+    m = re.search(r"first 16 hex digits\): `([0-9a-f]{16})`", text)
+    if not m or m.group(1) != csrc_digest():
+        return None
+    row = re.search(r"\| `k_%s` \| %s \| (\d+) \| (\d+) \| (\d+) \|" % (kernel, tile), text)
+    return int(row.group(3)) if row else None
 
 
 def measured_peaks():
@@ -325,7 +358,8 @@ def run_ours(args):
     k_ms, k_ev = kern[dom]
     achieved = k_ev * OPS_PER_EVAL[dom] / (k_ms * 1e-3) / 1e12
     roofline = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": peak_tops,
-                "unit": "TFLOP/s", "frac": achieved / peak_tops, "traffic": None,
+                "unit": "TFLOP/s", "frac": achieved / peak_tops,
+                "traffic": recorded_traffic(dom, f"{tile[0]}x{tile[1]}"),
                 "peak_source": (f"{sms} SMs x {FP32_LANES_PER_SM} FP32 lanes x {f_max / 1e6:.0f} "
                                 f"MHz ({peak_src} max SM clock), one op per lane per clock"),
                 "ops_per_eval": OPS_PER_EVAL[dom], "evals_per_launch": k_ev,
