@@ -74,6 +74,8 @@ def _load():
             lib.or_render_backward.argtypes = [_I64, _P, _P, _P, _P, _P, _P, _I64, _P, _P, _P, _P,
                                                _I, _I, _D, _D, _I, _I, _P, _P, _I64, _P, _P, _P,
                                                _P, _P, _P, _P, _P, _P, _P, _I]
+            lib.or_pose_gradient.argtypes = [_I64, _P, _P, _P, _P, _P, _P, _P, _P, _P]
+            lib.or_pose_gradient.restype = None
             lib.or_reach_pairs.argtypes = [_I64, _P, _P, _P, _P, _P, _I, _I, _D, _D, _P, _P, _P,
                                            _I64]
             lib.or_reach_pairs.restype = _I64
@@ -233,7 +235,8 @@ def render_backward(params, flip, order, T_ws, rows, cols, elev_min, elev_max, g
                     n_threads=0, pixels=None):
     """FP64 analytic gradient of L = sum gD*D + gN.N + gO*O (over the given pixels, or all).
     Returns dict with g_pos (n,3), g_logit (n,), g_quat (n,4), g_log_scale (n,2),
-    g_b (n,9) = (b_a, b_b, b_c) in the sensor frame, g_n (n,3), g_o (n,)."""
+    g_b (n,9) = (b_a, b_b, b_c) in the sensor frame, g_n (n,3), g_o (n,), and g_pose (6,) =
+    (dL/drho, dL/domega) for the left perturbation T^c_w <- exp(xi^) T^c_w, xi = (rho, omega)."""
     px = None if pixels is None else _c(pixels, np.int32).reshape(-1, 2)
     pos, logit, quat, ls = [_c(a, np.float64) for a in params]
     n = pos.shape[0]
@@ -260,6 +263,9 @@ def render_backward(params, flip, order, T_ws, rows, cols, elev_min, elev_max, g
         _ptr(gO_a), _ptr(out["g_pos"]), _ptr(out["g_logit"]),
         _ptr(out["g_quat"]), _ptr(out["g_log_scale"]), _ptr(out["g_b"]), _ptr(out["g_n"]),
         _ptr(out["g_o"]), n_threads)
+    out["g_pose"] = np.zeros(6)
+    _load().or_pose_gradient(n, _ptr(pos), _ptr(logit), _ptr(quat), _ptr(ls), _ptr(flip_a),
+                             _ptr(Tw), _ptr(out["g_b"]), _ptr(out["g_n"]), _ptr(out["g_pose"]))
     return out
 
 

@@ -58,7 +58,7 @@
 
 #define OR_PI 3.14159265358979323846
 
-int or_version(void) { return 6; }
+int or_version(void) { return 7; }
 
 /* ------------------------------------------------------------------------- */
 /* 1. pose                                                                   */
@@ -885,6 +885,39 @@ void or_render_backward(int64_t n, const double *pos, const double *logit, const
             g_quat[4 * i + k] = p->qlen > 0 ? (gqn[k] - p->q[k] * qg) / p->qlen : 0.0;
     }
     free(acc);
+    free(P);
+}
+
+/* Gradient with respect to the sensor pose, from the per-primitive sensor-frame gradients of
+ * or_render_backward.  The world-to-sensor transform enters only through b_a = s_a R t_a,
+ * b_b = s_b R t_b, b_c = R mu + t and n = +-R t_n (Supp. D.1; the tracking step of Sec. 3.3
+ * optimises this pose).  Perturbing it on the left, T^c_w <- exp(xi^) T^c_w with
+ * xi = (rho, omega) in the sensor frame, moves every point as b_c + omega x b_c + rho and every
+ * direction as b + omega x b, so
+ *   dL/drho = sum_i g_bc,i,
+ *   dL/domega = sum_i (b_c,i x g_bc,i + b_a,i x g_ba,i + b_b,i x g_bb,i + n_i x g_n,i).
+ * g_b is n x 9 (g_ba, g_bb, g_bc), g_n is n x 3; out = (dL/drho, dL/domega). */
+void or_pose_gradient(int64_t n, const double *pos, const double *logit, const double *quat,
+                      const double *log_scale, const int8_t *flip, const double *T_ws,
+                      const double *g_b, const double *g_n, double *out)
+{
+    or_prim *P = (or_prim *)malloc(sizeof(or_prim) * (size_t)(n > 0 ? n : 1));
+    prep_prims(n, pos, logit, quat, log_scale, flip, T_ws, P);
+    for (int k = 0; k < 6; ++k) out[k] = 0.0;
+    for (int64_t i = 0; i < n; ++i) {
+        const or_prim *p = &P[i];
+        const double *ga = g_b + 9 * i, *gb = g_b + 9 * i + 3, *gc = g_b + 9 * i + 6;
+        const double *gn = g_n + 3 * i;
+        double c1[3], c2[3], c3[3], c4[3];
+        cross3(p->bc, gc, c1);
+        cross3(p->ba, ga, c2);
+        cross3(p->bb, gb, c3);
+        cross3(p->n, gn, c4);
+        for (int k = 0; k < 3; ++k) {
+            out[k] += gc[k];
+            out[3 + k] += c1[k] + c2[k] + c3[k] + c4[k];
+        }
+    }
     free(P);
 }
 

@@ -118,3 +118,75 @@ def test_gradient_zero_outside_coverage(oracle_mod):
                                    v.elev_min, v.elev_max, mask, np.stack([mask] * 3), mask)
     for k in ("g_pos", "g_logit", "g_quat", "g_log_scale"):
         assert np.abs(g[k]).max() == 0.0
+
+
+def _se3_hat(xi):
+    rho, om = xi[:3], xi[3:]
+    X = np.zeros((4, 4))
+    X[:3, :3] = [[0.0, -om[2], om[1]], [om[2], 0.0, -om[0]], [-om[1], om[0], 0.0]]
+    X[:3, 3] = rho
+    return X
+
+
+@pytest.mark.parametrize("seed", [21, 22])
+def test_fd_pose_gradient(oracle_mod, seed):
+    """dL/dxi for the left perturbation T^c_w <- exp(xi^) T^c_w, xi = (rho, omega) in the sensor
+    frame, against central differences of the FP64 forward rendered at the perturbed pose (the
+    matrix exponential from scipy; same list order and normal signs)."""
+    linalg = pytest.importorskip("scipy.linalg")
+    scene = scenes.tiny_scene(14, seed, rows=10, cols=40, fov_deg=25, dist=(3.0, 6.0),
+                              log_scale=(-1.2, -0.6))
+    scene.pos_logit[:, 3] = np.minimum(scene.pos_logit[:, 3], math.log(0.9 / 0.1))
+    scene.views[0].T_ws = scenes.random_pose(np.random.default_rng(seed), 0.3, 10.0)
+    v = scene.views[0]
+    proj = oracle_mod.project_contract(scene.pos_logit, scene.quat, scene.log_scale, v.T_ws,
+                                       v.rows, v.cols, v.elev_min, v.elev_max)
+    flip, order = proj["flip"], oracle_mod.sort_order(proj["kappa"])
+    params = oracle_mod.split_params(scene.pos_logit, scene.quat, scene.log_scale)
+    rng = np.random.default_rng(seed + 100)
+    gD = rng.normal(size=(v.rows, v.cols))
+    gN = rng.normal(size=(3, v.rows, v.cols))
+    gO = rng.normal(size=(v.rows, v.cols))
+    an = oracle_mod.render_backward(params, flip, order, v.T_ws, v.rows, v.cols, v.elev_min,
+                                    v.elev_max, gD, gN, gO)["g_pose"]
+    T_cw = np.linalg.inv(v.T_ws)
+
+    def loss_at(xi):
+        T_ws = np.linalg.inv(linalg.expm(_se3_hat(xi)) @ T_cw)
+        out = oracle_mod.render(params, flip, order, T_ws, v.rows, v.cols, v.elev_min, v.elev_max)
+        return float((gD * out["D"]).sum() + (gN * out["N"]).sum() + (gO * out["O"]).sum()), \
+            out["n_contrib"]
+
+    _, nc0 = loss_at(np.zeros(6))
+    assert nc0.sum() > 20, "scene should be visible"
+    scale = np.abs(an).max()
+    checked = 0
+    for k in range(6):
+        h = 1e-6
+        xi = np.zeros(6)
+        xi[k] = h
+        Lp, ncp = loss_at(xi)
+        Lm, ncm = loss_at(-xi)
+        if not (np.array_equal(ncp, nc0) and np.array_equal(ncm, nc0)):
+            continue
+        fd = (Lp - Lm) / (2 * h)
+        assert abs(fd - an[k]) <= 2e-6 * max(abs(an[k]), 1e-3 * scale), (k, fd, an[k])
+        checked += 1
+    assert checked >= 5
+
+
+def test_pose_gradient_translation_part_is_centre_sum(oracle_mod):
+    """A pure translation of the sensor moves every centre by rho and no axis or normal: dL/drho
+    is the sum of the centres' sensor-frame gradients; the rotation part is not zero."""
+    scene = scenes.tiny_scene(6, 3, rows=10, cols=40, fov_deg=25, dist=(3.0, 6.0))
+    v = scene.views[0]
+    proj = oracle_mod.project_contract(scene.pos_logit, scene.quat, scene.log_scale, v.T_ws,
+                                       v.rows, v.cols, v.elev_min, v.elev_max)
+    params = oracle_mod.split_params(scene.pos_logit, scene.quat, scene.log_scale)
+    rng = np.random.default_rng(5)
+    g = oracle_mod.render_backward(params, proj["flip"], oracle_mod.sort_order(proj["kappa"]),
+                                   v.T_ws, v.rows, v.cols, v.elev_min, v.elev_max,
+                                   rng.normal(size=(10, 40)), rng.normal(size=(3, 10, 40)),
+                                   rng.normal(size=(10, 40)))
+    np.testing.assert_allclose(g["g_pose"][:3], g["g_b"][:, 6:9].sum(0), rtol=1e-12, atol=1e-12)
+    assert np.abs(g["g_pose"][3:]).max() > 0
