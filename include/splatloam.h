@@ -193,6 +193,23 @@ SPLAT_API int splat_render_backward(splat_ctx *ctx, const splat_gaussians *g,
                                     const float *dL_dalpha, float *g_pos_logit, float *g_quat,
                                     float *g_log_scale, int accumulate, void *stream);
 
+/* Gradient of the loss of the last backward (splat_render_views_backward, splat_render_backward
+ * or splat_refine_step) with respect to each registered view's pose, the tracking variable of
+ * Sec. 3.3.  The world-to-sensor transform T^c_w enters the render only through the sensor-frame
+ * vectors b_alpha = s_alpha R^c_w t_alpha, b_beta, b_c = R^c_w mu + t^c_w and the normal
+ * n = +-R^c_w t_n (Supp. D.1).  For the left perturbation T^c_w <- exp(xi^) T^c_w with
+ * xi = (rho, omega) in the sensor frame (rho a translation in metres, omega a rotation vector in
+ * radians), g_pose[6 v .. 6 v + 5] = (dL/drho, dL/domega) of view v at xi = 0:
+ *   dL/drho = sum_i dL/db_c,i,  dL/domega = sum_i (b_c x dL/db_c + b_alpha x dL/db_alpha +
+ *   b_beta x dL/db_beta + n x dL/dn)_i.
+ * g_pose: device, caller-owned, n_views x 6 floats.  Stream-ordered copy (graph-capturable).
+ * The backward forms these terms only while splat_set_pose_gradient(ctx, 1) is in effect (off
+ * by default: map refinement does not need them).
+ * Errors: INVALID_ARG (null), STATE (no backward with pose terms since the views were set),
+ * CUDA. */
+SPLAT_API int splat_set_pose_gradient(splat_ctx *ctx, int enable);
+SPLAT_API int splat_pose_gradient(splat_ctx *ctx, float *g_pose, void *stream);
+
 /* ---- loss and optimiser ------------------------------------------------------------------- */
 
 /* Per-pixel loss over n_pixels packed pixels (depth/alpha/target_depth [P], normal and

@@ -82,6 +82,8 @@ SIGNATURES = {
     "splat_adam_step": ([_P] * 13 + [_I64, ctypes.POINTER(splat_adam_config), _P], _I),
     "splat_refine_step": ([_P, _P, _P, _P, _I64, _P, _P, ctypes.POINTER(splat_loss_config),
                            ctypes.POINTER(splat_adam_config)] + [_P] * 9, _I),
+    "splat_set_pose_gradient": ([_P, _I], _I),
+    "splat_pose_gradient": ([_P, _P, _P], _I),
     "splat_get_status": ([_P, ctypes.POINTER(ctypes.c_uint32)], _I),
     "splat_get_stats": ([_P, ctypes.POINTER(splat_stats)], _I),
     "splat_debug_copy": ([_P, _I32, _P, _I64], _I64),

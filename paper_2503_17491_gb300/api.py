@@ -202,6 +202,19 @@ class SplatContext:
             _ptr(loss_out), _stream(stream)), "splat_refine_step")
 
     # ---- inspection ---------------------------------------------------------------------
+    def set_pose_gradient(self, on: bool):
+        """Make the following backward calls also form the per-view pose gradient."""
+        _lib.check(self.lib.splat_set_pose_gradient(self.h, 1 if on else 0),
+                   "splat_set_pose_gradient")
+
+    def pose_gradients(self, stream=None) -> torch.Tensor:
+        """(n_views, 6) float32 on the device: (dL/drho, dL/domega) of each view's pose for the
+        left perturbation T^c_w <- exp(xi^) T^c_w of the last backward (splat_pose_gradient)."""
+        out = torch.zeros(len(self.views), 6, dtype=torch.float32, device="cuda")
+        _lib.check(self.lib.splat_pose_gradient(self.h, _ptr(out), _stream(stream)),
+                   "splat_pose_gradient")
+        return out
+
     def status(self) -> int:
         f = ctypes.c_uint32(0)
         _lib.check(self.lib.splat_get_status(self.h, ctypes.byref(f)), "splat_get_status")

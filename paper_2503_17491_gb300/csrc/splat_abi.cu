@@ -92,6 +92,7 @@ struct splat_ctx {
     float *d_tfinal = nullptr;
     int32_t *d_nlast = nullptr;
     float4 *d_wgrad = nullptr;
+    float *d_pose = nullptr;        // per view (dL/drho, dL/domega) of the last backward
     float *d_img = nullptr;     // refine: depth, normal(3), alpha  (5 x max_pixels)
     float *d_gimg = nullptr;    // refine: their gradients
     uint32_t *d_counters = nullptr;             // [0] pairs M, [1] status, [2] queue f, [3] queue b
@@ -105,6 +106,8 @@ struct splat_ctx {
 
     // state of the last render
     bool rendered = false;
+    bool have_pose = false;         // a backward with pose terms ran since the views were set
+    bool want_pose = false;         // backward calls also accumulate the pose gradient
     int64_t last_n = 0;
     uint32_t *sorted_keys = nullptr, *sorted_vals = nullptr;
     uint32_t *entry_rect = nullptr;   // per list entry: rectangle inside its tile (K4)
@@ -216,6 +219,9 @@ int backward_core(splat_ctx *ctx, const splat_gaussians *g, const float *gD, con
 {
     uint32_t *cnt = ctx->d_counters;
     CK(cudaMemsetAsync(ctx->d_wgrad, 0, sizeof(float4) * 4 * static_cast<size_t>(g->n), st));
+    if (ctx->want_pose)
+        CK(cudaMemsetAsync(ctx->d_pose, 0, sizeof(float) * 6 * static_cast<size_t>(ctx->n_views),
+                           st));
     CK(cudaMemsetAsync(cnt + 3, 0, sizeof(uint32_t), st));
     CK(cudaMemsetAsync(ctx->d_evals + 1, 0, sizeof(unsigned long long), st));
     splat::RenderArgs a = render_args(ctx, g);
@@ -224,6 +230,7 @@ int backward_core(splat_ctx *ctx, const splat_gaussians *g, const float *gD, con
     a.g_alpha = gO;
     a.queue = cnt + 3;
     a.evals = ctx->d_evals + 1;
+    a.pose_grad = ctx->want_pose ? ctx->d_pose : nullptr;
     const bool prof = ctx->profiling && !capturing(st);
     if (prof) CK(cudaEventRecord(ctx->ev[2], st));
     CK(splat::launch_render_bwd(a, ctx->cfg.tile_h, ctx->cfg.tile_w, ctx->grid_bwd, st));
@@ -232,6 +239,7 @@ int backward_core(splat_ctx *ctx, const splat_gaussians *g, const float *gD, con
         ctx->rec_bwd = true;
     }
     ctx->launches += 1;
+    ctx->have_pose = ctx->want_pose;
     return SPLAT_OK;
 }
 
@@ -240,6 +248,7 @@ void free_ctx(splat_ctx *c)
     void *ptrs[] = {c->d_views, c->d_frames, c->d_tile_view, c->d_recs, c->d_dkeys, c->d_dvals,
                     c->d_dkeys2, c->d_dvals2, c->d_tkeys, c->d_tvals, c->d_tkeys2, c->d_tvals2,
                     c->d_block_sums, c->d_hist, c->d_ranges, c->d_tfinal, c->d_nlast, c->d_wgrad,
+                    c->d_pose,
                     c->d_img, c->d_gimg, c->d_counters, c->d_evals, c->d_pixframes,
                     c->d_tileinfo, c->d_tile_order};
     for (void *p : ptrs)
@@ -334,6 +343,7 @@ SPLAT_API int splat_ctx_create(const splat_render_config *cfg, const splat_capac
     if (e == cudaSuccess) e = dalloc(&c->d_tfinal, P);
     if (e == cudaSuccess) e = dalloc(&c->d_nlast, P);
     if (e == cudaSuccess) e = dalloc(&c->d_wgrad, static_cast<size_t>(cap->max_gaussians) * 4);
+    if (e == cudaSuccess) e = dalloc(&c->d_pose, static_cast<size_t>(cap->max_views) * 6);
     if (e == cudaSuccess) e = dalloc(&c->d_img, static_cast<size_t>(P) * 5);
     if (e == cudaSuccess) e = dalloc(&c->d_gimg, static_cast<size_t>(P) * 5);
     if (e == cudaSuccess) e = dalloc(&c->d_counters, 8);
@@ -527,6 +537,7 @@ SPLAT_API int splat_set_views(splat_ctx *ctx, int32_t n_views, const double *T_w
     ctx->n_pixels = pix;
     ctx->n_tiles = tiles;
     ctx->rendered = false;
+    ctx->have_pose = false;
     return SPLAT_OK;
 }
 
@@ -689,6 +700,23 @@ SPLAT_API int splat_refine_step(splat_ctx *ctx, float *pos_logit, float *quat, f
     CK(splat::launch_adam_fused(a, ctx->d_wgrad, st));
     CK(splat::launch_step_inc(step, st));
     ctx->launches += 3;   // loss, fused Adam, step counter
+    return SPLAT_OK;
+}
+
+SPLAT_API int splat_set_pose_gradient(splat_ctx *ctx, int enable)
+{
+    if (!ctx) return SPLAT_ERR_INVALID_ARG;
+    ctx->want_pose = enable != 0;
+    return SPLAT_OK;
+}
+
+SPLAT_API int splat_pose_gradient(splat_ctx *ctx, float *g_pose, void *stream)
+{
+    if (!ctx || !g_pose) return SPLAT_ERR_INVALID_ARG;
+    if (!ctx->have_pose) return SPLAT_ERR_STATE;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    CK(cudaMemcpyAsync(g_pose, ctx->d_pose, sizeof(float) * 6 * static_cast<size_t>(ctx->n_views),
+                       cudaMemcpyDeviceToDevice, st));
     return SPLAT_OK;
 }
 

@@ -306,6 +306,7 @@ struct RenderArgs {
     // backward inputs / outputs
     const float *g_depth, *g_normal, *g_alpha;
     float4 *wgrad;                // per primitive 4 x float4 (world-frame accumulators)
+    float *pose_grad;             // per view (dL/drho, dL/domega), or null
     uint32_t *queue;              // work counter (zeroed before each launch)
     unsigned long long *evals;    // evaluation counter
 };

@@ -807,6 +807,70 @@ __global__ void __launch_bounds__(kBlock, 3) k_render_bwd(const RenderArgs A)
                     atomicAdd(dst + 3, make_float4(gtn[0], gtn[1], gtn[2], 0.0f));
                 }
             }
+            if (A.pose_grad) {
+                // sensor-pose terms of the batch (left perturbation T^c_w <- exp(xi^) T^c_w):
+                // rho gets g_bc, omega gets b x g for the centre and both axes (tile frame) and
+                // n x g_n (sensor frame); summed over the warp, taken to the sensor frame by
+                // Q^T = R^c_w M^T
+                float v[16];
+#pragma unroll
+                for (int c = 0; c < 16; ++c) v[c] = 0.0f;
+                if (lane < cnt) {
+                    const float *a = acc[lane];
+                    const SlotRef st = slot_at(w, lane);
+                    v[0] = a[6];
+                    v[1] = a[7];
+                    v[2] = a[8];
+                    v[3] = (st.c.y * a[8] - st.c.z * a[7]) + (st.a.y * a[2] - st.a.z * a[1]) +
+                           (st.b.y * a[5] - st.b.z * a[4]);
+                    v[4] = (st.c.z * a[6] - st.c.x * a[8]) + (st.a.z * a[0] - st.a.x * a[2]) +
+                           (st.b.z * a[3] - st.b.x * a[5]);
+                    v[5] = (st.c.x * a[7] - st.c.y * a[6]) + (st.a.x * a[1] - st.a.y * a[0]) +
+                           (st.b.x * a[4] - st.b.y * a[3]);
+                    v[6] = st.n.y * a[11] - st.n.z * a[10];
+                    v[7] = st.n.z * a[9] - st.n.x * a[11];
+                    v[8] = st.n.x * a[10] - st.n.y * a[9];
+                }
+                // recursive halving over the warp: lane l < 16 ends with value reduced_index(l)
+#pragma unroll
+                for (int s = 0; s < 4; ++s) {
+                    const int m = 1 << s, half = 8 >> s;
+                    const bool up = (lane & m) != 0;
+#pragma unroll
+                    for (int k = 0; k < half; ++k) {
+                        const float send = up ? v[k] : v[k + half];
+                        const float keep = up ? v[k + half] : v[k];
+                        v[k] = keep + __shfl_xor_sync(kFull, send, m);
+                    }
+                }
+                const float tot = v[0] + __shfl_xor_sync(kFull, v[0], 16);
+                const int idx = ((lane & 1) ? 8 : 0) + ((lane & 2) ? 4 : 0) +
+                                ((lane & 4) ? 2 : 0) + ((lane & 8) ? 1 : 0);
+                float *scratch = reinterpret_cast<float *>(gwl);
+                if (lane < 16 && idx < 9) scratch[idx] = tot;
+                __syncwarp();
+                if (lane < 6) {
+                    const float *M = ti.M_hi;
+                    const float *R = ti.R;
+                    // y = M^T x (tile frame -> world-axis coordinates), z_k = (R y)_k
+                    const int part = lane < 3 ? 0 : 3, k = lane < 3 ? lane : lane - 3;
+                    float y[3];
+#pragma unroll
+                    for (int j = 0; j < 3; ++j)
+                        y[j] = M[j] * scratch[part] + M[3 + j] * scratch[part + 1] +
+                               M[6 + j] * scratch[part + 2];
+                    float z = R[3 * k] * y[0] + R[3 * k + 1] * y[1] + R[3 * k + 2] * y[2];
+                    if (part == 3) {
+                        // a cross product formed in the tile frame changes sign with det Q
+                        // (= det M; the frame (ray, h_x, h_y) is left-handed)
+                        const float det = M[0] * (M[4] * M[8] - M[5] * M[7]) -
+                                          M[1] * (M[3] * M[8] - M[5] * M[6]) +
+                                          M[2] * (M[3] * M[7] - M[4] * M[6]);
+                        z = (det < 0.0f ? -z : z) + scratch[6 + k];
+                    }
+                    atomicAdd(A.pose_grad + 6 * static_cast<int64_t>(ti.view) + lane, z);
+                }
+            }
             __syncwarp();
         };
 

@@ -34,13 +34,25 @@ def _grad_parity(s, tile=(16, 16), seed=0, label=""):
     g_ref = oracle.render_backward(params, flip, None, v.T_ws, v.rows, v.cols, v.elev_min,
                                    v.elev_max, gD, gN, gO, culled=cul)
     ctx = make_ctx(s.n, s.views, tile)
+    ctx.set_pose_gradient(True)
     pl, q, ls = to_dev(s)
     ctx.render(pl, q, ls)
     f = lambda a: torch.from_numpy(np.ascontiguousarray(a, np.float32)).cuda()  # noqa: E731
     g = ctx.backward(pl, q, ls, f(gD.ravel()), f(gN.reshape(3, -1)), f(gO.ravel()))
     torch.cuda.synchronize()
     got = gpu_grads_as_oracle(*g)
+    _pose_parity(ctx.pose_gradients()[0].double().cpu().numpy(), g_ref["g_pose"], label)
     return compare_grads(got, {k: g_ref[k] for k in got}, label), ctx
+
+
+def _pose_parity(got, ref, label=""):
+    """Pose gradient (dL/drho, dL/domega): each 3-vector within the gradient tolerance of the
+    oracle's, relative to its own norm."""
+    for part, sl in (("rho", slice(0, 3)), ("omega", slice(3, 6))):
+        nb = np.linalg.norm(ref[sl])
+        assert nb > 0, (label, part)
+        rel = np.linalg.norm(got[sl] - ref[sl]) / nb
+        assert rel <= 1e-3, (label, part, got[sl], ref[sl], rel)
 
 
 @pytest.mark.parametrize("tile", [(16, 16), (4, 64)])
@@ -234,3 +246,37 @@ def test_refine_step_reduces_loss_and_matches_plain():
     assert losses["batched"][0] == pytest.approx(losses["plain"][0], rel=1e-5)
     assert losses["batched"][-1] < losses["batched"][0]
     assert losses["plain"][-1] == pytest.approx(losses["batched"][-1], rel=2e-3)
+
+
+def test_pose_gradient_batched_views():
+    """Several views of uneven shapes in one backward: each view's pose gradient against the
+    oracle's for that view alone."""
+    s = scenes.workload(3, n=20_000)
+    views = [s.views[0], s.views[2], s.views[5]]
+    ctx = make_ctx(s.n, views)
+    ctx.set_pose_gradient(True)
+    pl, q, ls = to_dev(s)
+    ctx.render(pl, q, ls)
+    P = ctx.n_pixels
+    gD = np.zeros(P)
+    gN = np.zeros((3, P))
+    gO = np.zeros(P)
+    refs = []
+    for k, v in enumerate(views):
+        ref, params, flip, cul = oracle_view(s, v)
+        d, n, o = _upstream(v, ref["band"], 40 + k)
+        sl = slice(ctx.offsets[k], ctx.offsets[k] + v.n_pixels)
+        gD[sl], gN[:, sl], gO[sl] = d.ravel(), n.reshape(3, -1), o.ravel()
+        refs.append(oracle.render_backward(params, flip, None, v.T_ws, v.rows, v.cols,
+                                           v.elev_min, v.elev_max, d, n, o,
+                                           culled=cul)["g_pose"])
+    f = lambda a: torch.from_numpy(np.ascontiguousarray(a, np.float32)).cuda()  # noqa: E731
+    ctx.backward(pl, q, ls, f(gD), f(gN), f(gO))
+    got = ctx.pose_gradients().double().cpu().numpy()
+    for k in range(len(views)):
+        _pose_parity(got[k], refs[k], f"view {k}")
+    # off again: the next backward forms no pose terms and the copy is refused
+    ctx.set_pose_gradient(False)
+    ctx.backward(pl, q, ls, f(gD), f(gN), f(gO))
+    with pytest.raises(api._lib.SplatError):
+        ctx.pose_gradients()
