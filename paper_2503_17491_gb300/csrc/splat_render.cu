@@ -11,9 +11,9 @@
 // rectangle meets the warp's block -- and stages the entries that do, 32 at a time, into shared
 // memory.  A staged batch is then evaluated pair-parallel: the (primitive, pixel) candidates --
 // every pixel of the block inside a staged primitive's rectangle that is still live -- are
-// numbered primitive-major, and each round gives one candidate to every lane (a binary search
-// over the per-primitive prefix counts and a select of the pixel from the primitive's pixel
-// mask), so the intersection math runs on all 32 lanes whatever the primitives' footprints.
+// numbered primitive-major (a prefix sum of the per-primitive counts; each primitive's lane
+// writes its candidates into a shared list), and each round gives one candidate to every lane,
+// so the intersection math runs on all 32 lanes whatever the primitives' footprints.
 // Each pixel's lane then composites that round's hits on it in list order (front to back in the
 // forward, back to front in the backward), fetching them from the candidate lanes by shuffle.
 // A warp leaves its block as soon as all its pixels are saturated.
@@ -130,34 +130,6 @@ __device__ __forceinline__ uint32_t pixel_mask(uint32_t rect, int br, int bc)
     return (cols * 0x01010101u) & rows;
 }
 
-// position of the j-th (from 0) set bit of m; m has more than j set bits
-__device__ __forceinline__ int nth_bit(uint32_t m, int j)
-{
-    int pos = 0;
-    int c = __popc(m & 0xFFFFu);
-    if (j >= c) { j -= c; m >>= 16; pos += 16; }
-    c = __popc(m & 0xFFu);
-    if (j >= c) { j -= c; m >>= 8; pos += 8; }
-    c = __popc(m & 0xFu);
-    if (j >= c) { j -= c; m >>= 4; pos += 4; }
-    c = __popc(m & 0x3u);
-    if (j >= c) { j -= c; m >>= 2; pos += 2; }
-    if (j >= static_cast<int>(m & 1u)) pos += 1;
-    return pos;
-}
-
-// the largest lane b with off_b <= t (off is non-decreasing over the lanes and off_0 = 0)
-__device__ __forceinline__ int search_lane(int off, int t)
-{
-    int b = 0;
-#pragma unroll
-    for (int step = 16; step > 0; step >>= 1) {
-        const int o = __shfl_sync(kFull, off, b + step);
-        b = o <= t ? b + step : b;
-    }
-    return b;
-}
-
 // mask of the lanes t whose value key_t equals this lane's index (5 ballots over the key bits)
 __device__ __forceinline__ uint32_t lanes_keyed_to_me(bool valid, int key, int lane)
 {
@@ -216,7 +188,26 @@ struct WarpBatch {
     uint32_t pos[32];     // list position of the staged entry (backward: bit 31 = flipped)
     uint32_t prim[32];    // primitive index
     float4 p0[32], p1[32], p2[32], p3[32];
+    // the batch's candidates in numbering order: slot << 5 | pixel, bit 15 = a candidate (the
+    // backward's padding entries of a group carry their slot without it)
+    uint16_t cand[1024];
 };
+
+constexpr uint16_t kCandValid = 0x8000u;
+
+// write the candidates of slot `lane` (pixel mask m) at entries [first, first + span): the set
+// bits of m in increasing order, then padding entries that carry the slot only
+__device__ __forceinline__ void list_candidates(uint16_t *cand, uint32_t m, int first, int span,
+                                                int lane)
+{
+    int j = first;
+    while (m) {
+        const int px = __ffs(m) - 1;
+        m &= m - 1u;
+        cand[j++] = static_cast<uint16_t>(kCandValid | (lane << 5) | px);
+    }
+    for (; j < first + span; ++j) cand[j] = static_cast<uint16_t>(lane << 5);
+}
 
 struct WarpQueue {
     uint32_t p[64];      // pair id
@@ -408,15 +399,6 @@ __device__ __forceinline__ Numbering number_candidates(uint32_t m, int lane)
     return nb;
 }
 
-// candidate t of the batch: its primitive's slot b and its pixel l (meaningful when t < K)
-__device__ __forceinline__ void candidate(const Numbering &nb, int t, int &b, int &l)
-{
-    b = search_lane(nb.off, t);
-    const uint32_t mb = __shfl_sync(kFull, nb.m, b);
-    const int j = t - __shfl_sync(kFull, nb.off, b);
-    l = nth_bit(mb, j < 0 ? 0 : j);
-}
-
 // The backward numbers groups of four candidates instead: a primitive's pixels fill
 // ceil(n / 4) whole groups (off and K count groups), so that the four lanes of an aligned lane
 // group always belong to one primitive and its terms can be summed inside the group.
@@ -429,17 +411,6 @@ __device__ __forceinline__ Numbering number_groups(uint32_t m, int lane)
     nb.off = incl - n;
     nb.K = __shfl_sync(kFull, incl, 31);
     return nb;
-}
-
-// member q (0..3) of candidate group u: slot b, pixel l, and whether it is a candidate
-__device__ __forceinline__ bool group_member(const Numbering &nb, int u, int q, int &b, int &l)
-{
-    b = search_lane(nb.off, u);
-    const uint32_t mb = __shfl_sync(kFull, nb.m, b);
-    const int j = 4 * (u - __shfl_sync(kFull, nb.off, b)) + q;
-    const bool valid = u < nb.K && j >= 0 && j < __popc(mb);
-    l = nth_bit(mb, valid ? j : 0);
-    return valid;
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -455,7 +426,8 @@ template <int TH, int TW>
 __global__ void __launch_bounds__(kBlock, 3) k_render_fwd(const RenderArgs A)
 {
     static_assert(TH * TW == kBlock && TH % 4 == 0 && TW % 8 == 0, "4x8 warp blocks");
-    __shared__ FwdShared sh;
+    extern __shared__ __align__(16) unsigned char s_raw[];
+    FwdShared &sh = *reinterpret_cast<FwdShared *>(s_raw);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const uint32_t lt_mask = (1u << lane) - 1u;
     WarpBatch &w = sh.w[warp];
@@ -487,12 +459,13 @@ __global__ void __launch_bounds__(kBlock, 3) k_render_fwd(const RenderArgs A)
             }
             m &= __ballot_sync(kFull, !done);
             const Numbering nb = number_candidates(m, lane);
+            list_candidates(w.cand, m, nb.off, __popc(m), lane);
             __syncwarp();
             for (int r0 = 0; r0 < nb.K; r0 += 32) {
                 const int t = r0 + lane;
-                const bool valid = t < nb.K;
-                int b, l;
-                candidate(nb, t, b, l);
+                const uint32_t e = t < nb.K ? w.cand[t] : 0u;
+                const bool valid = (e & kCandValid) != 0u;
+                const int b = (e >> 5) & 31, l = e & 31;
                 Hit h;
                 h.a = h.d = 0.0f;
                 bool hit = false;
@@ -645,10 +618,13 @@ __global__ void __launch_bounds__(kBlock, 3) k_render_bwd(const RenderArgs A)
             m &= pixels_before_bound(lane < cnt ? static_cast<int>(q.pos[lane] & 0x7FFFFFFFu) : -1,
                                      nl, lane);
             const Numbering nb = number_groups(m, lane);
+            list_candidates(w.cand, m, 4 * nb.off, 4 * ((__popc(m) + 3) >> 2), lane);
             __syncwarp();
             for (int u0 = 0; u0 < nb.K; u0 += 8) {
-                int b, l;
-                const bool valid = group_member(nb, u0 + (lane >> 2), lane & 3, b, l);
+                const int t = 4 * u0 + lane;
+                const uint32_t e = t < 4 * nb.K ? w.cand[t] : (31u << 5);
+                const bool valid = (e & kCandValid) != 0u;
+                const int b = (e >> 5) & 31, l = e & 31;
                 const int k = static_cast<int>(w.pos[b] & 0x7FFFFFFFu);
                 const int nl_l = __shfl_sync(kFull, nl, l);
                 Hit h;
@@ -939,16 +915,16 @@ cudaError_t dispatch(int th, int tw, K k)
 
 }  // namespace
 
-cudaError_t launch_render_fwd(const RenderArgs &a, int tile_h, int tile_w, int grid,
-                              cudaStream_t st)
+// both kernels' shared memory is above the 48 KB static limit: allow it once per instantiation
+template <int TH, int TW>
+cudaError_t fwd_prepare()
 {
-    return dispatch(tile_h, tile_w, [&](auto TH, auto TW) {
-        k_render_fwd<decltype(TH)::value, decltype(TW)::value><<<grid, kBlock, 0, st>>>(a);
-        return cudaGetLastError();
-    });
+    static cudaError_t e = cudaFuncSetAttribute(k_render_fwd<TH, TW>,
+                                                cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                static_cast<int>(sizeof(FwdShared)));
+    return e;
 }
 
-// the backward's shared memory is above the 48 KB static limit: allow it once per instantiation
 template <int TH, int TW>
 cudaError_t bwd_prepare()
 {
@@ -956,6 +932,18 @@ cudaError_t bwd_prepare()
                                                 cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                 static_cast<int>(sizeof(BwdShared)));
     return e;
+}
+
+cudaError_t launch_render_fwd(const RenderArgs &a, int tile_h, int tile_w, int grid,
+                              cudaStream_t st)
+{
+    return dispatch(tile_h, tile_w, [&](auto TH, auto TW) {
+        constexpr int h = decltype(TH)::value, w = decltype(TW)::value;
+        const cudaError_t e = fwd_prepare<h, w>();
+        if (e != cudaSuccess) return e;
+        k_render_fwd<h, w><<<grid, kBlock, sizeof(FwdShared), st>>>(a);
+        return cudaGetLastError();
+    });
 }
 
 cudaError_t launch_render_bwd(const RenderArgs &a, int tile_h, int tile_w, int grid,
@@ -981,7 +969,10 @@ int render_occupancy(int tile_h, int tile_w, bool backward)
             return cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k_render_bwd<h, w>,
                                                                  kBlock, sizeof(BwdShared));
         }
-        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k_render_fwd<h, w>, kBlock, 0);
+        const cudaError_t e = fwd_prepare<h, w>();
+        if (e != cudaSuccess) return e;
+        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k_render_fwd<h, w>, kBlock,
+                                                             sizeof(FwdShared));
     });
     return blocks > 0 ? blocks : 1;
 }
