@@ -95,7 +95,8 @@ struct splat_ctx {
     float *d_pose = nullptr;        // per view (dL/drho, dL/domega) of the last backward
     float *d_img = nullptr;     // refine: depth, normal(3), alpha  (5 x max_pixels)
     float *d_gimg = nullptr;    // refine: their gradients
-    uint32_t *d_counters = nullptr;             // [0] pairs M, [1] status, [2] queue f, [3] queue b
+    uint32_t *d_counters = nullptr;   // [0] pairs M, [1] status, [2] queue f, [3] queue b,
+                                      // [4] (view, primitive) pairs that touch a tile
     unsigned long long *d_evals = nullptr;      // [0] forward, [1] backward
 
     // profiling events around the compositing kernels: [0,1] forward, [2,3] backward
@@ -167,6 +168,7 @@ int render_core(splat_ctx *ctx, const splat_gaussians *g, float *depth, float *n
     const int th = ctx->cfg.tile_h, tw = ctx->cfg.tile_w;
     uint32_t *cnt = ctx->d_counters;
     CK(cudaMemsetAsync(cnt, 0, sizeof(uint32_t), st));           // pair count
+    CK(cudaMemsetAsync(cnt + 4, 0, sizeof(uint32_t), st));       // pairs that touch a tile
     CK(cudaMemsetAsync(cnt + 2, 0, sizeof(uint32_t), st));       // forward queue
     CK(cudaMemsetAsync(ctx->d_evals, 0, sizeof(unsigned long long), st));
     CK(splat::launch_project(reinterpret_cast<const float4 *>(g->pos_logit),
@@ -174,12 +176,13 @@ int render_core(splat_ctx *ctx, const splat_gaussians *g, float *depth, float *n
                              reinterpret_cast<const float2 *>(g->log_scale), n, ctx->d_views,
                              ctx->n_views, ctx->cfg.sigma_cut, ctx->cfg.alpha_min, th, tw,
                              ctx->cfg.flip_normals,
-                             ctx->d_recs, ctx->d_dkeys, ctx->d_dvals, cnt + 1, st));
+                             ctx->d_recs, ctx->d_dkeys, ctx->d_dvals, cnt + 1, cnt + 4, st));
     uint32_t *dk, *dv;
     CK(splat::radix_sort_pairs(ctx->d_dkeys, ctx->d_dvals, ctx->d_dkeys2, ctx->d_dvals2, nullptr,
                                npv, 32, ctx->d_hist, &dk, &dv, st));
-    CK(splat::launch_emit(dv, npv, ctx->d_recs, ctx->d_views, n, th, tw, ctx->d_block_sums,
-                          ctx->d_tkeys, ctx->d_tvals, ctx->cap.max_pairs, cnt, cnt + 1, st));
+    CK(splat::launch_emit(dv, npv, cnt + 4, ctx->d_recs, ctx->d_views, n, th, tw,
+                          ctx->d_block_sums, ctx->d_tkeys, ctx->d_tvals, ctx->cap.max_pairs, cnt,
+                          cnt + 1, st));
     uint32_t *tk, *tv;
     CK(splat::radix_sort_pairs(ctx->d_tkeys, ctx->d_tvals, ctx->d_tkeys2, ctx->d_tvals2, cnt,
                                ctx->cap.max_pairs, bits_for(ctx->n_tiles), ctx->d_hist, &tk, &tv,

@@ -209,7 +209,7 @@ cudaError_t launch_project(const float4 *pos_logit, const float4 *quat, const fl
                            int64_t n, const ViewDesc *views, int n_views, float sigma,
                            float alpha_min, int tile_h, int tile_w, int flip_normals,
                            PairRec *recs, uint32_t *dkeys, uint32_t *dvals, uint32_t *status,
-                           cudaStream_t st);
+                           uint32_t *n_valid, cudaStream_t st);
 
 // stable LSD radix sort of (uint32 key, uint32 value) pairs on key bits [0, bits);
 // the count is read on the device from *d_count (clamped to max_n); result lands in
@@ -223,10 +223,12 @@ cudaError_t radix_sort_pairs(uint32_t *keys, uint32_t *vals, uint32_t *keys_alt,
 
 // offsets of every sorted pair, emission of (global tile, pair id) entries, total pair count
 constexpr int kScanGrid = 304;
-cudaError_t launch_emit(const uint32_t *sorted_pair_ids, int64_t n_pairs_total, const PairRec *recs,
-                        const ViewDesc *views, int64_t n_per_view, int tile_h, int tile_w,
-                        uint32_t *block_sums, uint32_t *tile_keys, uint32_t *tile_vals,
-                        int64_t max_pairs, uint32_t *d_count, uint32_t *status, cudaStream_t st);
+// n_valid: device count of the leading sorted pairs that touch a tile (the rest touch none)
+cudaError_t launch_emit(const uint32_t *sorted_pair_ids, int64_t n_pairs_total,
+                        const uint32_t *n_valid, const PairRec *recs, const ViewDesc *views,
+                        int64_t n_per_view, int tile_h, int tile_w, uint32_t *block_sums,
+                        uint32_t *tile_keys, uint32_t *tile_vals, int64_t max_pairs,
+                        uint32_t *d_count, uint32_t *status, cudaStream_t st);
 
 // Pixel rectangle of a (view, primitive) record inside tile (tr, tc) of a tile_h x tile_w
 // tiling, packed as 4 bytes (r_lo, r_hi, c_lo, c_hi) with the record's normal-flip bit in bit 31;

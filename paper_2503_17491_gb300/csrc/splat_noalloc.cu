@@ -271,10 +271,11 @@ extern "C" SPLAT_API int splat_render_noalloc(const splat_gaussians *g,
                                 reinterpret_cast<const float2 *>(g->log_scale), n, view, 1,
                                 cfg.sigma_cut, cfg.alpha_min, th, tw, cfg.flip_normals, recs, dkeys,
                                 dvals,
-                                cnt + 1, st));
+                                cnt + 1, cnt + 4, st));
     uint32_t *dk, *dv;
     NA_CK(splat::radix_sort_pairs(dkeys, dvals, dkeys2, dvals2, nullptr, n, 32, hist, &dk, &dv, st));
-    NA_CK(splat::launch_emit(dv, n, recs, view, n, th, tw, block_sums, tkeys, tvals, kMaxPairs, cnt,
+    NA_CK(splat::launch_emit(dv, n, cnt + 4, recs, view, n, th, tw, block_sums, tkeys, tvals,
+                             kMaxPairs, cnt,
                              cnt + 1, st));
     uint32_t *tk, *tv;
     NA_CK(splat::radix_sort_pairs(tkeys, tvals, tkeys2, tvals2, cnt, kMaxPairs, bits_for(n_tiles),

@@ -282,7 +282,8 @@ __global__ void __launch_bounds__(256) k_project(
     const float2 *__restrict__ log_scale, int64_t n, const ViewDesc *__restrict__ views,
     int n_views, float sigma, float alpha_min, int tile_h, int tile_w, int flip_normals,
     PairRec *__restrict__ recs,
-    uint32_t *__restrict__ dkeys, uint32_t *__restrict__ dvals, uint32_t *__restrict__ status)
+    uint32_t *__restrict__ dkeys, uint32_t *__restrict__ dvals, uint32_t *__restrict__ status,
+    uint32_t *__restrict__ n_valid)
 {
     const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
     if (i >= n) return;
@@ -317,6 +318,7 @@ __global__ void __launch_bounds__(256) k_project(
     }
     const v3 mu{pl.x, pl.y, pl.z};
 
+    uint32_t nv = 0;   // pairs of this primitive that touch a tile
     for (int v = 0; v < n_views; ++v) {
         const ViewDesc &vd = views[v];
         const int64_t p = static_cast<int64_t>(v) * n + i;
@@ -340,7 +342,13 @@ __global__ void __launch_bounds__(256) k_project(
         recs[p] = rec;
         dkeys[p] = (rec.cf & kCountMask) ? __float_as_uint(rec.kappa) : 0xFFFFFFFFu;
         dvals[p] = static_cast<uint32_t>(p);
+        nv += (rec.cf & kCountMask) ? 1u : 0u;
     }
+    // the number of pairs that touch a tile: after the range sort they lead (the others carry
+    // the key 0xFFFFFFFF), so the emission stops there
+    const unsigned am = __activemask();
+    const unsigned s = __reduce_add_sync(am, nv);
+    if ((threadIdx.x & 31) == __ffs(am) - 1 && s) atomicAdd(n_valid, s);
 }
 
 }  // namespace
@@ -349,13 +357,13 @@ cudaError_t launch_project(const float4 *pos_logit, const float4 *quat, const fl
                            int64_t n, const ViewDesc *views, int n_views, float sigma,
                            float alpha_min, int tile_h, int tile_w, int flip_normals,
                            PairRec *recs, uint32_t *dkeys, uint32_t *dvals, uint32_t *status,
-                           cudaStream_t st)
+                           uint32_t *n_valid, cudaStream_t st)
 {
     if (n <= 0) return cudaSuccess;
     const unsigned grid = static_cast<unsigned>((n + 255) / 256);
     k_project<<<grid, 256, 0, st>>>(pos_logit, quat, log_scale, n, views, n_views, sigma,
                                     alpha_min, tile_h, tile_w, flip_normals, recs, dkeys, dvals,
-                                    status);
+                                    status, n_valid);
     return cudaGetLastError();
 }
 

@@ -201,10 +201,12 @@ __device__ __forceinline__ uint32_t pair_count(const PairRec *recs, uint32_t p)
 
 // per-CTA sums of the tile counts of its chunk of sorted pairs
 __global__ void __launch_bounds__(kThreads) k_count_sums(const uint32_t *__restrict__ sorted,
-                                                         int64_t n, const PairRec *__restrict__ recs,
+                                                         int64_t n_total, const uint32_t *n_valid,
+                                                         const PairRec *__restrict__ recs,
                                                          uint32_t *__restrict__ block_sums)
 {
     __shared__ unsigned long long s_sum[kWarps];
+    const int64_t n = clamp_count(n_valid, n_total);
     const int64_t chunk = (n + gridDim.x - 1) / gridDim.x;
     const int64_t b = chunk * blockIdx.x;
     const int64_t e = b + chunk < n ? b + chunk : n;
@@ -252,7 +254,8 @@ __global__ void __launch_bounds__(1024) k_scan_sums(uint32_t *__restrict__ block
 
 // each thread emits the tiles of consecutive sorted pairs; offsets from a CTA scan
 __global__ void __launch_bounds__(kThreads) k_emit(
-    const uint32_t *__restrict__ sorted, int64_t n, const PairRec *__restrict__ recs,
+    const uint32_t *__restrict__ sorted, int64_t n_total, const uint32_t *n_valid,
+    const PairRec *__restrict__ recs,
     const ViewDesc *__restrict__ views, int64_t n_per_view, int tile_h, int tile_w,
     const uint32_t *__restrict__ block_base, uint32_t *__restrict__ tile_keys,
     uint32_t *__restrict__ tile_vals, int64_t max_pairs)
@@ -260,6 +263,7 @@ __global__ void __launch_bounds__(kThreads) k_emit(
     __shared__ uint32_t s_warp[kWarps];
     __shared__ uint32_t s_carry;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int64_t n = clamp_count(n_valid, n_total);
     const int64_t chunk = (n + gridDim.x - 1) / gridDim.x;
     const int64_t b = chunk * blockIdx.x;
     const int64_t e = b + chunk < n ? b + chunk : n;
@@ -398,14 +402,17 @@ cudaError_t radix_sort_pairs(uint32_t *keys, uint32_t *vals, uint32_t *keys_alt,
     return cudaGetLastError();
 }
 
-cudaError_t launch_emit(const uint32_t *sorted_pair_ids, int64_t n_pairs_total, const PairRec *recs,
-                        const ViewDesc *views, int64_t n_per_view, int tile_h, int tile_w,
-                        uint32_t *block_sums, uint32_t *tile_keys, uint32_t *tile_vals,
-                        int64_t max_pairs, uint32_t *d_count, uint32_t *status, cudaStream_t st)
+cudaError_t launch_emit(const uint32_t *sorted_pair_ids, int64_t n_pairs_total,
+                        const uint32_t *n_valid, const PairRec *recs, const ViewDesc *views,
+                        int64_t n_per_view, int tile_h, int tile_w, uint32_t *block_sums,
+                        uint32_t *tile_keys, uint32_t *tile_vals, int64_t max_pairs,
+                        uint32_t *d_count, uint32_t *status, cudaStream_t st)
 {
-    k_count_sums<<<kScanGrid, kThreads, 0, st>>>(sorted_pair_ids, n_pairs_total, recs, block_sums);
+    k_count_sums<<<kScanGrid, kThreads, 0, st>>>(sorted_pair_ids, n_pairs_total, n_valid, recs,
+                                                  block_sums);
     k_scan_sums<<<1, 1024, 0, st>>>(block_sums, kScanGrid, max_pairs, d_count, status);
-    k_emit<<<kScanGrid, kThreads, 0, st>>>(sorted_pair_ids, n_pairs_total, recs, views, n_per_view,
+    k_emit<<<kScanGrid, kThreads, 0, st>>>(sorted_pair_ids, n_pairs_total, n_valid, recs, views,
+                                           n_per_view,
                                            tile_h, tile_w, block_sums, tile_keys, tile_vals,
                                            max_pairs);
     return cudaGetLastError();
