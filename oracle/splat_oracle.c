@@ -58,7 +58,7 @@
 
 #define OR_PI 3.14159265358979323846
 
-int or_version(void) { return 7; }
+int or_version(void) { return 8; }
 
 /* ------------------------------------------------------------------------- */
 /* 1. pose                                                                   */
@@ -248,19 +248,13 @@ static int contract_bbox(f3 ba, f3 bb, f3 bc, float o, float alpha_min, float si
     f3 A = { a * ba.x, a * ba.y, a * ba.z };
     f3 B = { a * bb.x, a * bb.y, a * bb.z };
     f3 C = bc;
-    float uv[16];
-    int nv;
-    if (k < 2.0f) {
-        float c = k - 1.0f;
-        float t[16] = { 1.0f, -c, 1.0f, c, c, 1.0f, -c, 1.0f,
-                        -1.0f, c, -1.0f, -c, -c, -1.0f, c, -1.0f };
-        memcpy(uv, t, sizeof t);
-        nv = 8;
-    } else {
-        float t[8] = { -1.0f, -1.0f, 1.0f, -1.0f, 1.0f, 1.0f, -1.0f, 1.0f };
-        memcpy(uv, t, sizeof t);
-        nv = 4;
-    }
+    /* the octagon (|u|, |v| <= 1, |u| + |v| <= k in units of a); when the diamond misses the
+     * square's corners (k >= 2) the cut c = 1 repeats each corner, and the repeated vertices
+     * give zero-length edges that add nothing */
+    const int nv = 8;
+    float c = k < 2.0f ? k - 1.0f : 1.0f;
+    float uv[16] = { 1.0f, -c, 1.0f, c, c, 1.0f, -c, 1.0f,
+                     -1.0f, c, -1.0f, -c, -c, -1.0f, c, -1.0f };
     f3 P[8];
     for (int i = 0; i < nv; ++i) {
         float u = uv[2 * i], v = uv[2 * i + 1];
@@ -335,15 +329,13 @@ static int contract_bbox(f3 ba, f3 bb, f3 bc, float o, float alpha_min, float si
          * extreme vertices follow from the signs of cross products, one arctangent each,
          * relative to the centre direction */
         float gc = or_contract_atan2f(C.y, C.x);
-        int imin = 0, imax = 0;
+        float xmin = P[0].x, ymin = P[0].y, xmax = P[0].x, ymax = P[0].y;
         for (int i = 1; i < nv; ++i) {
-            if (P[imax].x * P[i].y - P[imax].y * P[i].x > 0.0f) imax = i;
-            if (P[imin].x * P[i].y - P[imin].y * P[i].x < 0.0f) imin = i;
+            if (xmax * P[i].y - ymax * P[i].x > 0.0f) { xmax = P[i].x; ymax = P[i].y; }
+            if (xmin * P[i].y - ymin * P[i].x < 0.0f) { xmin = P[i].x; ymin = P[i].y; }
         }
-        float dmax = or_contract_atan2f(C.x * P[imax].y - C.y * P[imax].x,
-                                        C.x * P[imax].x + C.y * P[imax].y);
-        float dmin = or_contract_atan2f(C.x * P[imin].y - C.y * P[imin].x,
-                                        C.x * P[imin].x + C.y * P[imin].y);
+        float dmax = or_contract_atan2f(C.x * ymax - C.y * xmax, C.x * xmax + C.y * ymax);
+        float dmin = or_contract_atan2f(C.x * ymin - C.y * xmin, C.x * xmin + C.y * ymin);
         float glo = gc + dmin, ghi = gc + dmax;
         float kc = (float)W / C_TWO_PI;
         float uf = ((C_PI - ghi) * kc - 0.5f) - eps;

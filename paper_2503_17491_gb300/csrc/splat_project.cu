@@ -149,33 +149,17 @@ __device__ uint32_t contract_bbox(v3 ba, v3 bb, v3 bc, float o, float alpha_min,
     const v3 A{a * ba.x, a * ba.y, a * ba.z};
     const v3 B{a * bb.x, a * bb.y, a * bb.z};
     const v3 C = bc;
-    float u[8], w[8];
-    int nv;
-    if (k < 2.0f) {
-        const float c = k - 1.0f;
-        u[0] = 1.0f;  w[0] = -c;
-        u[1] = 1.0f;  w[1] = c;
-        u[2] = c;     w[2] = 1.0f;
-        u[3] = -c;    w[3] = 1.0f;
-        u[4] = -1.0f; w[4] = c;
-        u[5] = -1.0f; w[5] = -c;
-        u[6] = -c;    w[6] = -1.0f;
-        u[7] = c;     w[7] = -1.0f;
-        nv = 8;
-    } else {
-        u[0] = -1.0f; w[0] = -1.0f;
-        u[1] = 1.0f;  w[1] = -1.0f;
-        u[2] = 1.0f;  w[2] = 1.0f;
-        u[3] = -1.0f; w[3] = 1.0f;
-        nv = 4;
-    }
+    // the octagon (|u|, |w| <= 1, |u| + |w| <= k in units of a); when the diamond misses the
+    // square's corners (k >= 2) the cut c = 1 repeats each corner, and the repeated vertices give
+    // zero-length edges that add nothing
+    const float c = k < 2.0f ? k - 1.0f : 1.0f;
+    const float u[8] = {1.0f, 1.0f, c, -c, -1.0f, -1.0f, -c, c};
+    const float w[8] = {-c, c, 1.0f, 1.0f, c, -c, -1.0f, -1.0f};
     v3 P[8];
 #pragma unroll
-    for (int i = 0; i < 8; ++i) {
-        if (i < nv)
-            P[i] = v3{(C.x + u[i] * A.x) + w[i] * B.x, (C.y + u[i] * A.y) + w[i] * B.y,
-                      (C.z + u[i] * A.z) + w[i] * B.z};
-    }
+    for (int i = 0; i < 8; ++i)
+        P[i] = v3{(C.x + u[i] * A.x) + w[i] * B.x, (C.y + u[i] * A.y) + w[i] * B.y,
+                  (C.z + u[i] * A.z) + w[i] * B.z};
 
     // does the z axis cross the polygon's xy-shadow?  c + u A + w B = 0 with |u|, |w| <= 1 and
     // |u| + |w| <= k
@@ -205,8 +189,9 @@ __device__ uint32_t contract_bbox(v3 ba, v3 bb, v3 bc, float o, float alpha_min,
     // ordered by z / |xy| without a division (z_i r_j against z_j r_i); one arctangent each
     float zh = 0.0f, rh = 0.0f, zl = 0.0f, rl = 0.0f;
     bool have = false;
-    for (int i = 0; i < nv; ++i) {
-        const v3 p = P[i], q = P[(i + 1) % nv];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        const v3 p = P[i], q = P[(i + 1) & 7];
         elev_candidate(p.z, sqrtf(p.x * p.x + p.y * p.y), zh, rh, zl, rl, have);
         const v3 d{q.x - p.x, q.y - p.y, q.z - p.z};
         const float pd = p.x * d.x + p.y * d.y;
@@ -244,15 +229,14 @@ __device__ uint32_t contract_bbox(v3 ba, v3 bb, v3 bc, float o, float alpha_min,
         // extreme vertices follow from the signs of cross products, one arctangent each,
         // relative to the centre direction
         const float gc = contract_atan2(C.y, C.x);
-        int imin = 0, imax = 0;
-        for (int i = 1; i < nv; ++i) {
-            if (P[imax].x * P[i].y - P[imax].y * P[i].x > 0.0f) imax = i;
-            if (P[imin].x * P[i].y - P[imin].y * P[i].x < 0.0f) imin = i;
+        float xmin = P[0].x, ymin = P[0].y, xmax = P[0].x, ymax = P[0].y;
+#pragma unroll
+        for (int i = 1; i < 8; ++i) {
+            if (xmax * P[i].y - ymax * P[i].x > 0.0f) { xmax = P[i].x; ymax = P[i].y; }
+            if (xmin * P[i].y - ymin * P[i].x < 0.0f) { xmin = P[i].x; ymin = P[i].y; }
         }
-        const float dmax = contract_atan2(C.x * P[imax].y - C.y * P[imax].x,
-                                          C.x * P[imax].x + C.y * P[imax].y);
-        const float dmin = contract_atan2(C.x * P[imin].y - C.y * P[imin].x,
-                                          C.x * P[imin].x + C.y * P[imin].y);
+        const float dmax = contract_atan2(C.x * ymax - C.y * xmax, C.x * xmax + C.y * ymax);
+        const float dmin = contract_atan2(C.x * ymin - C.y * xmin, C.x * xmin + C.y * ymin);
         const float glo = gc + dmin, ghi = gc + dmax;
         const float kc = static_cast<float>(W) / kTwoPi;
         const float uf = ((kPi - ghi) * kc - 0.5f) - kPixelMargin;
