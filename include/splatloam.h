@@ -172,8 +172,10 @@ SPLAT_API int splat_render_views(splat_ctx *ctx, const splat_gaussians *g, float
  * in the packed layout (NULL means zero).  Writes g_pos_logit (n x 4: dL/dmu, dL/dlogit),
  * g_quat (n x 4, w.r.t. the unnormalised quaternion) and g_log_scale (n x 2), summed over all
  * views; accumulate = 1 adds to the existing contents instead of overwriting.  The back-to-front
- * pass replays each pixel's composite, recovers the transmittance by division and reduces each
- * primitive's per-pixel terms in a warp before one set of atomics per (tile, primitive).
+ * pass (Supp. D.2) replays, for each pixel, exactly the contributions the forward composited (the
+ * forward records them per 4 x 8 pixel block in the context's workspace), recovers the
+ * transmittance by division and sums each primitive's per-pixel terms before one set of atomics
+ * per (block, primitive).
  * Errors: INVALID_ARG, STATE (no render before), CUDA. */
 SPLAT_API int splat_render_views_backward(splat_ctx *ctx, const splat_gaussians *g,
                                           const float *dL_ddepth, const float *dL_dnormal,

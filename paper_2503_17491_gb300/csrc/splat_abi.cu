@@ -93,10 +93,14 @@ struct splat_ctx {
     int32_t *d_nlast = nullptr;
     float4 *d_wgrad = nullptr;
     float *d_pose = nullptr;        // per view (dL/drho, dL/domega) of the last backward
+    uint2 *d_rec = nullptr;         // contributor records: chunks of 32 (forward -> backward)
+    uint32_t *d_rec_prev = nullptr, *d_rec_head = nullptr, *d_rec_fill = nullptr;
+    uint32_t rec_cap = 0;           // chunks in the record pool
     float *d_img = nullptr;     // refine: depth, normal(3), alpha  (5 x max_pixels)
     float *d_gimg = nullptr;    // refine: their gradients
     uint32_t *d_counters = nullptr;   // [0] pairs M, [1] status, [2] queue f, [3] queue b,
-                                      // [4] (view, primitive) pairs that touch a tile
+                                      // [4] (view, primitive) pairs that touch a tile,
+                                      // [5] record chunks taken
     unsigned long long *d_evals = nullptr;      // [0] forward, [1] backward
 
     // profiling events around the compositing kernels: [0,1] forward, [2,3] backward
@@ -146,6 +150,13 @@ splat::RenderArgs render_args(splat_ctx *ctx, const splat_gaussians *g)
     a.tile_order = ctx->d_tile_order;
     a.sorted_vals = ctx->sorted_vals;
     a.entry_rect = ctx->entry_rect;
+    a.rec = ctx->d_rec;
+    a.rec_prev = ctx->d_rec_prev;
+    a.rec_alloc = ctx->d_counters + 5;
+    a.rec_cap = ctx->rec_cap;
+    a.rec_head = ctx->d_rec_head;
+    a.rec_fill = ctx->d_rec_fill;
+    a.status = ctx->d_counters + 1;
     a.n_tiles = ctx->n_tiles;
     a.n_items = ctx->n_tiles * (splat::kBlock / 32);
     a.alpha_min = ctx->cfg.alpha_min;
@@ -168,7 +179,7 @@ int render_core(splat_ctx *ctx, const splat_gaussians *g, float *depth, float *n
     const int th = ctx->cfg.tile_h, tw = ctx->cfg.tile_w;
     uint32_t *cnt = ctx->d_counters;
     CK(cudaMemsetAsync(cnt, 0, sizeof(uint32_t), st));           // pair count
-    CK(cudaMemsetAsync(cnt + 4, 0, sizeof(uint32_t), st));       // pairs that touch a tile
+    CK(cudaMemsetAsync(cnt + 4, 0, 2 * sizeof(uint32_t), st));   // touching pairs, chunks
     CK(cudaMemsetAsync(cnt + 2, 0, sizeof(uint32_t), st));       // forward queue
     CK(cudaMemsetAsync(ctx->d_evals, 0, sizeof(unsigned long long), st));
     CK(splat::launch_project(reinterpret_cast<const float4 *>(g->pos_logit),
@@ -251,7 +262,7 @@ void free_ctx(splat_ctx *c)
     void *ptrs[] = {c->d_views, c->d_frames, c->d_tile_view, c->d_recs, c->d_dkeys, c->d_dvals,
                     c->d_dkeys2, c->d_dvals2, c->d_tkeys, c->d_tvals, c->d_tkeys2, c->d_tvals2,
                     c->d_block_sums, c->d_hist, c->d_ranges, c->d_tfinal, c->d_nlast, c->d_wgrad,
-                    c->d_pose,
+                    c->d_pose, c->d_rec, c->d_rec_prev, c->d_rec_head, c->d_rec_fill,
                     c->d_img, c->d_gimg, c->d_counters, c->d_evals, c->d_pixframes,
                     c->d_tileinfo, c->d_tile_order};
     for (void *p : ptrs)
@@ -347,6 +358,15 @@ SPLAT_API int splat_ctx_create(const splat_render_config *cfg, const splat_capac
     if (e == cudaSuccess) e = dalloc(&c->d_nlast, P);
     if (e == cudaSuccess) e = dalloc(&c->d_wgrad, static_cast<size_t>(cap->max_gaussians) * 4);
     if (e == cudaSuccess) e = dalloc(&c->d_pose, static_cast<size_t>(cap->max_views) * 6);
+    // contributor records: at most one per (block, staged entry); the pool takes two per
+    // (tile, primitive) pair of capacity plus one partial chunk per work item
+    const int64_t items = TT * (splat::kBlock / 32);
+    const int64_t chunks = (2 * M + 31) / 32 + items;
+    c->rec_cap = static_cast<uint32_t>(chunks < 0xFFFFFFF0ll ? chunks : 0xFFFFFFF0ll);
+    if (e == cudaSuccess) e = dalloc(&c->d_rec, static_cast<size_t>(c->rec_cap) * 32);
+    if (e == cudaSuccess) e = dalloc(&c->d_rec_prev, static_cast<size_t>(c->rec_cap));
+    if (e == cudaSuccess) e = dalloc(&c->d_rec_head, static_cast<size_t>(items));
+    if (e == cudaSuccess) e = dalloc(&c->d_rec_fill, static_cast<size_t>(items));
     if (e == cudaSuccess) e = dalloc(&c->d_img, static_cast<size_t>(P) * 5);
     if (e == cudaSuccess) e = dalloc(&c->d_gimg, static_cast<size_t>(P) * 5);
     if (e == cudaSuccess) e = dalloc(&c->d_counters, 8);

@@ -310,6 +310,13 @@ struct RenderArgs {
     float4 *wgrad;                // per primitive 4 x float4 (world-frame accumulators)
     float *pose_grad;             // per view (dL/drho, dL/domega), or null
     uint32_t *queue;              // work counter (zeroed before each launch)
+    // contributor records (forward writes, backward reads; see splat_render.cu)
+    uint2 *rec;                   // pool of 32-record chunks, or null (no records)
+    uint32_t *rec_prev;           // per chunk: the item's previous chunk
+    uint32_t *rec_alloc;          // chunks taken (zeroed before the forward)
+    uint32_t rec_cap;             // chunks in the pool
+    uint32_t *rec_head, *rec_fill;   // per work item: last chunk and its fill
+    uint32_t *status;             // status bits
     unsigned long long *evals;    // evaluation counter
 };
 

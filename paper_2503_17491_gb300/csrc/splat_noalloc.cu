@@ -296,6 +296,7 @@ extern "C" SPLAT_API int splat_render_noalloc(const splat_gaussians *g,
     a.tile_order = order;
     a.sorted_vals = tv;
     a.entry_rect = rects;
+    a.status = cnt + 1;   // no contributor records (forward only)
     a.n_tiles = n_tiles;
     a.n_items = n_tiles * (splat::kBlock / 32);
     a.alpha_min = cfg.alpha_min;

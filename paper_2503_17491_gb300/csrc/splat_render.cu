@@ -36,8 +36,10 @@
 // skipped below alpha_min, stop before T < t_min, and max |s_hat| <= sigma written as
 // max(|p_x|, |p_y|) <= sigma |p_z| so that misses need no division.
 //
-// Forward and backward evaluate a pair with the same explicitly rounded operations, so the
-// backward replays exactly the contributor set of the forward.  The backward recovers
+// Forward and backward evaluate a pair with the same explicitly rounded operations.  The forward
+// records, per work item, the staged primitives that contributed with the mask of the pixels they
+// contributed to (contributor records, below); the backward walks those records back to front, so
+// it evaluates exactly the forward's contributing pairs and no others.  The backward recovers
 // T_k = T_{k+1} / (1 - alpha_k) from the final transmittance and keeps the suffix sums B_{d,k},
 // B_{n,k}, B_{o,k} of Supp. D.2 in the pixel's lane; the pixel lane hands dL/dalpha_k and the
 // blending weight back to the candidate lane, which forms the pair's 13 geometric terms.  The
@@ -142,33 +144,6 @@ __device__ __forceinline__ uint32_t lanes_keyed_to_me(bool valid, int key, int l
     return m;
 }
 
-// For slots ordered by strictly decreasing list position k_b (lanes b >= cnt pass k = -1) and a
-// bound nl per pixel lane: the mask of pixel lanes l with k_b < nl_l, returned to lane b.  Each
-// pixel finds how many leading slots lie at or past its bound (a binary search), and lane b
-// compares all 32 counts with b at once, bit-sliced over the counts' six bits.
-__device__ __forceinline__ uint32_t pixels_before_bound(int k, int nl, int b)
-{
-    int t = 0;
-#pragma unroll
-    for (int step = 16; step > 0; step >>= 1) {
-        const int kk = __shfl_sync(kFull, k, t + step - 1);
-        t = kk >= nl ? t + step : t;
-    }
-    t += __shfl_sync(kFull, k, 31) >= nl && t == 31 ? 1 : 0;
-    uint32_t lt = 0u, eq = kFull;
-#pragma unroll
-    for (int s = 5; s >= 0; --s) {
-        const uint32_t bits = __ballot_sync(kFull, (t >> s) & 1);
-        if ((b >> s) & 1) {
-            lt |= eq & ~bits;
-            eq &= bits;
-        } else {
-            eq &= ~bits;
-        }
-    }
-    return lt | eq;   // pixels whose count t_l <= b
-}
-
 // inclusive warp prefix sum
 __device__ __forceinline__ int warp_incl_scan(int v, int lane)
 {
@@ -191,6 +166,7 @@ struct WarpBatch {
     // the batch's candidates in numbering order: slot << 5 | pixel, bit 15 = a candidate (the
     // backward's padding entries of a group carry their slot without it)
     uint16_t cand[1024];
+    uint32_t hits[32];    // forward: the block's pixels each slot contributed to
 };
 
 constexpr uint16_t kCandValid = 0x8000u;
@@ -413,6 +389,47 @@ __device__ __forceinline__ Numbering number_groups(uint32_t m, int lane)
     return nb;
 }
 
+// Contributor records.  The forward appends, per work item and in list order, one record per
+// staged primitive that contributed to a pixel of the block: (pair id | normal-flip bit 31,
+// mask of the block's pixels it contributed to).  Records go to chunks of 32 taken from a pool by
+// an atomic counter; each chunk links to the item's previous one, and the item keeps its last
+// chunk and that chunk's fill.  The backward walks an item's chunks from the last, each chunk
+// (read back to front) being one batch, so it evaluates exactly the pairs that contributed.
+constexpr uint32_t kNoChunk = 0xFFFFFFFFu;
+
+// append the records of the lanes with `have` (in lane order) to the item's chain
+__device__ __forceinline__ void append_records(const RenderArgs &A, bool have, uint2 r, int lane,
+                                               uint32_t &chain, int &fill)
+{
+    const uint32_t bal = __ballot_sync(kFull, have);
+    const int nh = __popc(bal);
+    if (nh == 0 || fill < 0) return;
+    const int rank = __popc(bal & ((1u << lane) - 1u));
+    const int room = chain == kNoChunk ? 0 : 32 - fill;
+    if (nh <= room) {
+        if (have) A.rec[static_cast<int64_t>(chain) * 32 + fill + rank] = r;
+        fill += nh;
+        return;
+    }
+    uint32_t c = 0;
+    if (lane == 0) c = atomicAdd(A.rec_alloc, 1u);
+    c = __shfl_sync(kFull, c, 0);
+    if (c >= A.rec_cap) {   // pool exhausted: the backward of this item would be incomplete
+        if (lane == 0) atomicOr(A.status, SPLAT_STATUS_CAPACITY);
+        fill = -1;
+        return;
+    }
+    if (lane == 0) A.rec_prev[c] = chain;
+    if (have) {
+        if (rank < room)
+            A.rec[static_cast<int64_t>(chain) * 32 + fill + rank] = r;
+        else
+            A.rec[static_cast<int64_t>(c) * 32 + (rank - room)] = r;
+    }
+    chain = c;
+    fill = nh - room;
+}
+
 // ---------------------------------------------------------------------------------------------
 // forward
 // ---------------------------------------------------------------------------------------------
@@ -448,10 +465,13 @@ __global__ void __launch_bounds__(kBlock, 3) k_render_fwd(const RenderArgs A)
         float T = 1.0f, D = 0.0f, N0 = 0.0f, N1 = 0.0f, N2 = 0.0f, O = 0.0f;
         int last = 0;
         bool done = !bp.inside;
+        uint32_t chain = kNoChunk;   // this item's last record chunk
+        int fill = 0;                 // records in it
 
         // stage queue entries [0, cnt) and composite them, round by round
         auto composite = [&](int cnt) {
             uint32_t m = 0u;
+            w.hits[lane] = 0u;
             if (lane < cnt) {
                 stage(A, ti, q.p[lane], (q.pos[lane] >> 31) != 0, q.rect[lane], w, lane);
                 w.pos[lane] = q.pos[lane] & 0x7FFFFFFFu;
@@ -497,12 +517,20 @@ __global__ void __launch_bounds__(kBlock, 3) k_render_fwd(const RenderArgs A)
                             O = __fadd_rn(O, wgt);
                             T = tt;
                             last = static_cast<int>(w.pos[bs]) + 1;
+                            atomicOr(&w.hits[bs], 1u << lane);
                         }
                     }
                 }
                 if (__all_sync(kFull, done)) break;
             }
             __syncwarp();
+            // contributor records of the batch (slots with at least one contribution), in list
+            // order, for the backward
+            if (A.rec) {
+                const uint32_t hm = lane < cnt ? w.hits[lane] : 0u;
+                const uint2 r = make_uint2(q.p[lane] | (q.pos[lane] & 0x80000000u), hm);
+                append_records(A, hm != 0u, r, lane, chain, fill);
+            }
         };
 
         int qn = 0;
@@ -533,6 +561,10 @@ __global__ void __launch_bounds__(kBlock, 3) k_render_fwd(const RenderArgs A)
             }
         }
         if (qn > 0 && !__all_sync(kFull, done)) composite(qn);
+        if (A.rec && lane == 0) {   // an item whose records overflowed the pool keeps none
+            A.rec_head[item] = fill < 0 ? kNoChunk : chain;
+            A.rec_fill[item] = fill < 0 ? 0u : static_cast<uint32_t>(fill);
+        }
         if (bp.inside) {
             A.depth[bp.out] = D;
             A.normal[bp.out] = N0;
@@ -554,7 +586,6 @@ struct BwdShared {
     float acc[kWarps][32][kAcc];
     float2 gw[kWarps][32];   // per candidate lane: (dL/dalpha, blending weight) from its pixel
     TileInfo ti[kWarps];
-    WarpQueue q[kWarps];
 };
 
 template <int TH, int TW>
@@ -564,12 +595,10 @@ __global__ void __launch_bounds__(kBlock, 3) k_render_bwd(const RenderArgs A)
     extern __shared__ __align__(16) unsigned char s_raw[];
     BwdShared &sh = *reinterpret_cast<BwdShared *>(s_raw);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const uint32_t gt_mask = ~((2u << lane) - 1u);   // lanes above this one
     WarpBatch &w = sh.w[warp];
     float(*acc)[kAcc] = sh.acc[warp];
     float2 *gwl = sh.gw[warp];
     TileInfo &ti = sh.ti[warp];
-    WarpQueue &q = sh.q[warp];
     unsigned long long evals = 0;
 
     for (;;) {
@@ -581,12 +610,9 @@ __global__ void __launch_bounds__(kBlock, 3) k_render_bwd(const RenderArgs A)
         load_tile(A.tiles, tile, ti, lane);
         const BlockPix bp = block_pixel<TH, TW>(ti, blk, lane);
         put_pix(w, lane, load_pix(A.pixframes, bp.inside ? bp.pf : ti.pix_base));
-        const uint2 rg = A.ranges[tile];
         float T = 1.0f, gD = 0.0f, gN0 = 0.0f, gN1 = 0.0f, gN2 = 0.0f, gO = 0.0f;
-        int nl = 0;
         if (bp.inside) {
             T = A.t_final[bp.out];
-            nl = A.n_last[bp.out];
             if (A.g_depth) gD = A.g_depth[bp.out];
             if (A.g_normal) {
                 gN0 = A.g_normal[bp.out];
@@ -596,27 +622,19 @@ __global__ void __launch_bounds__(kBlock, 3) k_render_bwd(const RenderArgs A)
             if (A.g_alpha) gO = A.g_alpha[bp.out];
         }
         float Y = 0.0f;   // sum over channels of g_ch B_ch (suffix sums of Supp. D.2)
-        // the warp's bound: nothing at or past it contributes to any of its pixels
-        int wl = nl;
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) wl = max(wl, __shfl_xor_sync(kFull, wl, o));
-        const uint32_t live = __ballot_sync(kFull, nl > 0);
 
-        // stage queue entries [0, cnt) (in decreasing list order), replay and differentiate them
-        // round by round, then flush each staged primitive's sums (lane b flushes slot b)
-        auto adjoint = [&](int cnt) {
+        // stage the batch's records (slot l = record r of lane l: pair id | flip, contributed
+        // pixels), replay and differentiate them round by round, then flush each staged
+        // primitive's sums (lane b flushes slot b)
+        auto adjoint = [&](int cnt, uint2 r) {
             uint32_t m = 0u;
             if (lane < cnt) {
-                w.prim[lane] = stage(A, ti, q.p[lane], (q.pos[lane] >> 31) != 0, q.rect[lane],
-                                     w, lane);
-                w.pos[lane] = q.pos[lane];
+                w.prim[lane] = stage(A, ti, r.x & 0x7FFFFFFFu, (r.x >> 31) != 0, 0u, w, lane);
+                w.pos[lane] = r.x & 0x80000000u;
 #pragma unroll
                 for (int c = 0; c < kAcc; ++c) acc[lane][c] = 0.0f;
-                m = pixel_mask(q.rect[lane], bp.br, bp.bc) & live;
+                m = r.y;
             }
-            // a pixel takes part only in slots before its last contributor
-            m &= pixels_before_bound(lane < cnt ? static_cast<int>(q.pos[lane] & 0x7FFFFFFFu) : -1,
-                                     nl, lane);
             const Numbering nb = number_groups(m, lane);
             list_candidates(w.cand, m, 4 * nb.off, 4 * ((__popc(m) + 3) >> 2), lane);
             __syncwarp();
@@ -625,13 +643,11 @@ __global__ void __launch_bounds__(kBlock, 3) k_render_bwd(const RenderArgs A)
                 const uint32_t e = t < 4 * nb.K ? w.cand[t] : (31u << 5);
                 const bool valid = (e & kCandValid) != 0u;
                 const int b = (e >> 5) & 31, l = e & 31;
-                const int k = static_cast<int>(w.pos[b] & 0x7FFFFFFFu);
-                const int nl_l = __shfl_sync(kFull, nl, l);
                 Hit h;
                 h.a = h.d = 0.0f;
                 h.clamped = false;
                 bool hit = false;
-                if (valid && k < nl_l) {
+                if (valid) {
                     ++evals;
                     hit = evaluate(slot_at(w, b), get_pix(w, l), A.sigma, A.alpha_min,
                                    A.alpha_max, h);
@@ -850,33 +866,16 @@ __global__ void __launch_bounds__(kBlock, 3) k_render_bwd(const RenderArgs A)
             __syncwarp();
         };
 
-        int qn = 0;
-        for (int ch = ((wl - 1) >> 5) << 5; ch >= 0 && wl > 0; ch -= 32) {
-            const int jl = ch + lane;   // list position of this lane's entry
-            bool rel = false, flip = false;
-            uint32_t p = 0, rect = 0;
-            if (jl < wl) rel = read_entry<TH, TW>(A, ti, rg.x + jl, bp, p, rect, flip);
-            const uint32_t m = __ballot_sync(kFull, rel);
-            if (rel) {   // queue in decreasing list position: higher lanes first
-                const int pos = qn + __popc(m & gt_mask);
-                q.p[pos] = p;
-                q.rect[pos] = rect;
-                q.pos[pos] = static_cast<uint32_t>(jl) | (flip ? 0x80000000u : 0u);
-            }
-            qn += __popc(m);
-            __syncwarp();
-            if (qn >= 32) {
-                adjoint(32);
-                if (lane < qn - 32) {
-                    q.p[lane] = q.p[32 + lane];
-                    q.rect[lane] = q.rect[32 + lane];
-                    q.pos[lane] = q.pos[32 + lane];
-                }
-                qn -= 32;
-                __syncwarp();
-            }
+        // the item's record chunks, last first; each chunk read back to front is one batch
+        uint32_t chunk = A.rec_head[item];
+        int cnt = static_cast<int>(A.rec_fill[item]);
+        while (chunk != kNoChunk) {
+            uint2 r = make_uint2(0u, 0u);
+            if (lane < cnt) r = A.rec[static_cast<int64_t>(chunk) * 32 + (cnt - 1 - lane)];
+            adjoint(cnt, r);
+            chunk = A.rec_prev[chunk];
+            cnt = 32;
         }
-        if (qn > 0) adjoint(qn);
     }
     warp_count(evals, A.evals);
 }
