@@ -116,6 +116,7 @@ struct splat_ctx {
     int64_t last_n = 0;
     uint32_t *sorted_keys = nullptr, *sorted_vals = nullptr;
     uint32_t *entry_rect = nullptr;   // per list entry: rectangle inside its tile (K4)
+    uint8_t *entry_blocks = nullptr;  // per list entry: 4 x 8 blocks it meets (K4)
 };
 
 namespace {
@@ -150,6 +151,7 @@ splat::RenderArgs render_args(splat_ctx *ctx, const splat_gaussians *g)
     a.tile_order = ctx->d_tile_order;
     a.sorted_vals = ctx->sorted_vals;
     a.entry_rect = ctx->entry_rect;
+    a.entry_blocks = ctx->entry_blocks;
     a.rec = ctx->d_rec;
     a.rec_prev = ctx->d_rec_prev;
     a.rec_alloc = ctx->d_counters + 5;
@@ -189,8 +191,9 @@ int render_core(splat_ctx *ctx, const splat_gaussians *g, float *depth, float *n
                              ctx->cfg.flip_normals,
                              ctx->d_recs, ctx->d_dkeys, ctx->d_dvals, cnt + 1, cnt + 4, st));
     uint32_t *dk, *dv;
+    // the range sort drops the pairs that touch no tile (key 0xFFFFFFFF) in its first pass
     CK(splat::radix_sort_pairs(ctx->d_dkeys, ctx->d_dvals, ctx->d_dkeys2, ctx->d_dvals2, nullptr,
-                               npv, 32, ctx->d_hist, &dk, &dv, st));
+                               npv, 32, ctx->d_hist, &dk, &dv, st, cnt + 4));
     CK(splat::launch_emit(dv, npv, cnt + 4, ctx->d_recs, ctx->d_views, n, th, tw,
                           ctx->d_block_sums, ctx->d_tkeys, ctx->d_tvals, ctx->cap.max_pairs, cnt,
                           cnt + 1, st));
@@ -198,14 +201,17 @@ int render_core(splat_ctx *ctx, const splat_gaussians *g, float *depth, float *n
     CK(splat::radix_sort_pairs(ctx->d_tkeys, ctx->d_tvals, ctx->d_tkeys2, ctx->d_tvals2, cnt,
                                ctx->cap.max_pairs, bits_for(ctx->n_tiles), ctx->d_hist, &tk, &tv,
                                st));
-    // the tile sort's other value buffer is free: it takes the entries' tile rectangles
+    // the tile sort's other buffers are free: they take the entries' tile rectangles and the
+    // blocks each meets
     uint32_t *rects = tv == ctx->d_tvals ? ctx->d_tvals2 : ctx->d_tvals;
+    uint8_t *blocks = reinterpret_cast<uint8_t *>(tk == ctx->d_tkeys ? ctx->d_tkeys2 : ctx->d_tkeys);
     CK(splat::launch_ranges(tk, tv, ctx->d_recs, ctx->d_tileinfo, th, tw, cnt,
-                            ctx->cap.max_pairs, ctx->d_ranges, ctx->n_tiles, rects, st));
+                            ctx->cap.max_pairs, ctx->d_ranges, ctx->n_tiles, rects, blocks, st));
     CK(splat::launch_order_tiles(ctx->d_ranges, ctx->n_tiles, ctx->d_tile_order, st));
     ctx->sorted_keys = tk;
     ctx->sorted_vals = tv;
     ctx->entry_rect = rects;
+    ctx->entry_blocks = blocks;
     splat::RenderArgs a = render_args(ctx, g);
     a.depth = depth;
     a.normal = normal;

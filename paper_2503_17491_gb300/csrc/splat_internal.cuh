@@ -217,9 +217,13 @@ cudaError_t launch_project(const float4 *pos_logit, const float4 *quat, const fl
 constexpr int kSortGrid = 304;
 constexpr int kSortTile = 2048;   // keys per CTA tile (256 threads x 8)
 constexpr int kHistWords = kSortGrid * 256 + 256;   // per-CTA digit counts + digit totals
+// With d_count_kept non-null the first pass also drops every item whose key is 0xFFFFFFFF (which
+// would sort last) and the later passes sort the d_count_kept items left, which the caller has
+// counted beforehand.
 cudaError_t radix_sort_pairs(uint32_t *keys, uint32_t *vals, uint32_t *keys_alt, uint32_t *vals_alt,
                              const uint32_t *d_count, int64_t max_n, int bits, uint32_t *tmp_hist,
-                             uint32_t **keys_out, uint32_t **vals_out, cudaStream_t st);
+                             uint32_t **keys_out, uint32_t **vals_out, cudaStream_t st,
+                             const uint32_t *d_count_kept = nullptr);
 
 // offsets of every sorted pair, emission of (global tile, pair id) entries, total pair count
 constexpr int kScanGrid = 304;
@@ -275,12 +279,28 @@ __device__ __forceinline__ uint32_t tile_local_rect(const PairRec &rec, int tr, 
            ((rec.cf & kPairFlip) ? kRectFlip : 0u);
 }
 
+// Which of a tile's 4 x 8 pixel blocks (bit (row block) * tile_w / 8 + column block) a rectangle
+// inside the tile (tile_local_rect) meets.
+__device__ __forceinline__ uint32_t rect_blocks(uint32_t rect, int tile_h, int tile_w)
+{
+    const int r_lo = rect & 0xFF, r_hi = (rect >> 8) & 0xFF;
+    const int c_lo = (rect >> 16) & 0x3F, c_hi = (rect >> 24) & 0x3F;
+    if (r_lo > r_hi || r_hi >= tile_h) return 0u;
+    const int wc = tile_w / 8;
+    const uint32_t cols = ((2u << (c_hi >> 3)) - 1u) & ~((1u << (c_lo >> 3)) - 1u);
+    uint32_t m = 0u;
+    for (int rb = r_lo >> 2; rb <= r_hi >> 2; ++rb) m |= cols << (rb * wc);
+    return m;
+}
+
 // K4: [start, end) per tile from the sorted tile ids, and every list entry's pixel rectangle
-// inside its tile (tile_local_rect) in entry_rect
+// inside its tile (tile_local_rect) in entry_rect and the 4 x 8 blocks it meets (rect_blocks) in
+// entry_blocks
 cudaError_t launch_ranges(const uint32_t *tile_keys, const uint32_t *tile_vals,
                           const PairRec *recs, const TileInfo *tiles, int tile_h, int tile_w,
                           const uint32_t *d_count, int64_t max_pairs, uint2 *ranges,
-                          int64_t n_tiles, uint32_t *entry_rect, cudaStream_t st);
+                          int64_t n_tiles, uint32_t *entry_rect, uint8_t *entry_blocks,
+                          cudaStream_t st);
 
 // tiles ordered by decreasing log2 of their list length (order inside a bucket unspecified)
 cudaError_t launch_order_tiles(const uint2 *ranges, int64_t n_tiles, uint32_t *order,
@@ -297,6 +317,7 @@ struct RenderArgs {
     const uint32_t *tile_order;   // tiles in decreasing order of list length (work order)
     const uint32_t *sorted_vals;  // pair ids in (tile, range, id) order
     const uint32_t *entry_rect;   // per list entry: pixel rectangle inside its tile, flip bit
+    const uint8_t *entry_blocks;  // per list entry: the 4 x 8 blocks of its tile it meets
     int64_t n_tiles;
     int64_t n_items;              // n_tiles x blocks per tile
     float alpha_min, alpha_max, t_min, sigma;

@@ -280,9 +280,10 @@ extern "C" SPLAT_API int splat_render_noalloc(const splat_gaussians *g,
     uint32_t *tk, *tv;
     NA_CK(splat::radix_sort_pairs(tkeys, tvals, tkeys2, tvals2, cnt, kMaxPairs, bits_for(n_tiles),
                                   hist, &tk, &tv, st));
-    uint32_t *rects = tv == tvals ? tvals2 : tvals;   // the tile sort's free value buffer
+    uint32_t *rects = tv == tvals ? tvals2 : tvals;   // the tile sort's free buffers
+    uint8_t *blocks = reinterpret_cast<uint8_t *>(tk == tkeys ? tkeys2 : tkeys);
     NA_CK(splat::launch_ranges(tk, tv, recs, tiles, th, tw, cnt, kMaxPairs, ranges, n_tiles, rects,
-                               st));
+                               blocks, st));
     NA_CK(splat::launch_order_tiles(ranges, n_tiles, order, st));
 
     splat::RenderArgs a{};
@@ -296,6 +297,7 @@ extern "C" SPLAT_API int splat_render_noalloc(const splat_gaussians *g,
     a.tile_order = order;
     a.sorted_vals = tv;
     a.entry_rect = rects;
+    a.entry_blocks = blocks;
     a.status = cnt + 1;   // no contributor records (forward only)
     a.n_tiles = n_tiles;
     a.n_items = n_tiles * (splat::kBlock / 32);

@@ -344,17 +344,17 @@ __device__ __forceinline__ BlockPix block_pixel(const TileInfo &ti, int blk, int
     return b;
 }
 
-// read one list entry per lane: pair id, rectangle inside the tile, whether it meets the block
-template <int TH, int TW>
-__device__ __forceinline__ bool read_entry(const RenderArgs &A, const TileInfo &ti, uint32_t j,
-                                           const BlockPix &bp, uint32_t &p, uint32_t &rect,
-                                           bool &flip)
+// read one list entry per lane if it meets the warp's block blk: pair id, rectangle inside the
+// tile, normal flip
+__device__ __forceinline__ bool read_entry(const RenderArgs &A, uint32_t j, int blk, uint32_t &p,
+                                           uint32_t &rect, bool &flip)
 {
+    if (!((A.entry_blocks[j] >> blk) & 1u)) return false;
     p = A.sorted_vals[j];
     const uint32_t r = A.entry_rect[j];
     flip = (r & kRectFlip) != 0u;
     rect = r & ~kRectFlip;
-    return pixel_mask(rect, bp.br, bp.bc) != 0u;
+    return true;
 }
 
 // Candidate numbering of a staged batch: lane b holds its primitive's live-pixel mask m, the
@@ -539,7 +539,7 @@ __global__ void __launch_bounds__(kBlock, 3) k_render_fwd(const RenderArgs A)
             const uint32_t j = ch + lane;
             bool rel = false, flip = false;
             uint32_t p = 0, rect = 0;
-            if (j < rg.y) rel = read_entry<TH, TW>(A, ti, j, bp, p, rect, flip);
+            if (j < rg.y) rel = read_entry(A, j, blk, p, rect, flip);
             const uint32_t m = __ballot_sync(kFull, rel);
             if (rel) {
                 const int pos = qn + __popc(m & lt_mask);

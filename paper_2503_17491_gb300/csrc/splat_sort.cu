@@ -41,7 +41,8 @@ __device__ __forceinline__ int64_t clamp_count(const uint32_t *d_count, int64_t 
 // per-CTA digit histogram: hist[digit * grid + cta]
 __global__ void __launch_bounds__(kThreads) k_upsweep(const uint32_t *__restrict__ keys,
                                                       const uint32_t *d_count, int64_t max_n,
-                                                      int shift, uint32_t *__restrict__ hist)
+                                                      int shift, int drop_max,
+                                                      uint32_t *__restrict__ hist)
 {
     __shared__ uint32_t s_cnt[kWarps][kRadix];
     const int tid = threadIdx.x, warp = tid >> 5;
@@ -51,8 +52,10 @@ __global__ void __launch_bounds__(kThreads) k_upsweep(const uint32_t *__restrict
     const int64_t chunk = chunk_of(n, gridDim.x);
     const int64_t begin = chunk * blockIdx.x;
     const int64_t end = begin + chunk < n ? begin + chunk : n;
-    for (int64_t j = begin + tid; j < end; j += kThreads)
-        atomicAdd(&s_cnt[warp][(keys[j] >> shift) & 0xFF], 1u);
+    for (int64_t j = begin + tid; j < end; j += kThreads) {
+        const uint32_t k = keys[j];
+        if (!(drop_max && k == 0xFFFFFFFFu)) atomicAdd(&s_cnt[warp][(k >> shift) & 0xFF], 1u);
+    }
     __syncthreads();
     uint32_t t = 0;
 #pragma unroll
@@ -88,13 +91,15 @@ __global__ void __launch_bounds__(256) k_scan_digits(uint32_t *__restrict__ hist
 __global__ void __launch_bounds__(kThreads) k_downsweep(
     const uint32_t *__restrict__ keys_in, const uint32_t *__restrict__ vals_in,
     uint32_t *__restrict__ keys_out, uint32_t *__restrict__ vals_out, const uint32_t *d_count,
-    int64_t max_n, int shift, const uint32_t *__restrict__ hist, const uint32_t *__restrict__ dtot)
+    int64_t max_n, int shift, int drop_max, const uint32_t *__restrict__ hist,
+    const uint32_t *__restrict__ dtot)
 {
     __shared__ uint32_t s_base[kRadix];          // running global offset per digit
     __shared__ uint32_t s_wcnt[kWarps][kRadix];  // per-warp digit counts -> warp prefixes
     __shared__ uint32_t s_tile[kRadix];          // digit totals of the current tile
     __shared__ uint32_t s_toff[kRadix];          // digit offsets inside the current tile
     __shared__ uint32_t s_wsum[kWarps];
+    __shared__ uint32_t s_kept;                  // items of the current tile that are written
     __shared__ uint32_t s_key[kSortTile], s_val[kSortTile];   // the tile, sorted by digit
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int64_t n = clamp_count(d_count, max_n);
@@ -127,8 +132,8 @@ __global__ void __launch_bounds__(kThreads) k_downsweep(
 #pragma unroll
         for (int it = 0; it < kItems; ++it) {
             const int64_t j = tb + warp * (32 * kItems) + it * 32 + lane;
-            const bool valid = j < end;
-            key[it] = valid ? keys_in[j] : 0u;
+            key[it] = j < end ? keys_in[j] : 0u;
+            const bool valid = j < end && !(drop_max && key[it] == 0xFFFFFFFFu);
             val[it] = valid ? vals_in[j] : 0u;
             dig[it] = valid ? static_cast<int>((key[it] >> shift) & 0xFF) : kRadix + lane;
             const uint32_t peers = __match_any_sync(0xFFFFFFFFu, dig[it]);
@@ -162,6 +167,7 @@ __global__ void __launch_bounds__(kThreads) k_downsweep(
             uint32_t wbase = 0;
             for (int w = 0; w < warp; ++w) wbase += s_wsum[w];
             s_toff[tid] = wbase + x - run;
+            if (tid == kRadix - 1) s_kept = wbase + x;
         }
         __syncthreads();
         // sort the tile by digit in shared memory (stable: warp, item, lane order) ...
@@ -176,7 +182,7 @@ __global__ void __launch_bounds__(kThreads) k_downsweep(
         __syncthreads();
         // ... and write each digit's run to its global place: consecutive threads, consecutive
         // addresses
-        const int cnt = static_cast<int>(end - tb < kSortTile ? end - tb : kSortTile);
+        const int cnt = static_cast<int>(s_kept);
         for (int i = tid; i < cnt; i += kThreads) {
             const uint32_t k = s_key[i];
             const int d = static_cast<int>((k >> shift) & 0xFF);
@@ -324,7 +330,8 @@ __global__ void __launch_bounds__(kThreads) k_emit(
 __global__ void k_ranges(const uint32_t *__restrict__ keys, const uint32_t *__restrict__ vals,
                          const PairRec *__restrict__ recs, const TileInfo *__restrict__ tiles,
                          int tile_h, int tile_w, const uint32_t *d_count, int64_t max_pairs,
-                         uint2 *__restrict__ ranges, uint32_t *__restrict__ entry_rect)
+                         uint2 *__restrict__ ranges, uint32_t *__restrict__ entry_rect,
+                         uint8_t *__restrict__ entry_blocks)
 {
     const int64_t m = clamp_count(d_count, max_pairs);
     for (int64_t j = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; j < m;
@@ -333,7 +340,9 @@ __global__ void k_ranges(const uint32_t *__restrict__ keys, const uint32_t *__re
         if (j == 0 || keys[j - 1] != t) ranges[t].x = static_cast<uint32_t>(j);
         if (j == m - 1 || keys[j + 1] != t) ranges[t].y = static_cast<uint32_t>(j + 1);
         const TileInfo &ti = tiles[t];
-        entry_rect[j] = tile_local_rect(recs[vals[j]], ti.tr, ti.tc, ti.cols, tile_h, tile_w);
+        const uint32_t r = tile_local_rect(recs[vals[j]], ti.tr, ti.tc, ti.cols, tile_h, tile_w);
+        entry_rect[j] = r;
+        entry_blocks[j] = static_cast<uint8_t>(rect_blocks(r & ~kRectFlip, tile_h, tile_w));
     }
 }
 
@@ -379,16 +388,21 @@ cudaError_t launch_order_tiles(const uint2 *ranges, int64_t n_tiles, uint32_t *o
 
 cudaError_t radix_sort_pairs(uint32_t *keys, uint32_t *vals, uint32_t *keys_alt, uint32_t *vals_alt,
                              const uint32_t *d_count, int64_t max_n, int bits, uint32_t *tmp_hist,
-                             uint32_t **keys_out, uint32_t **vals_out, cudaStream_t st)
+                             uint32_t **keys_out, uint32_t **vals_out, cudaStream_t st,
+                             const uint32_t *d_count_kept)
 {
     uint32_t *kin = keys, *vin = vals, *kout = keys_alt, *vout = vals_alt;
     if (max_n > 0) {
         for (int shift = 0; shift < bits; shift += 8) {
             uint32_t *dtot = tmp_hist + kSortGrid * kRadix;
-            k_upsweep<<<kSortGrid, kThreads, 0, st>>>(kin, d_count, max_n, shift, tmp_hist);
+            // with d_count_kept, the first pass drops the key 0xFFFFFFFF and the later passes
+            // sort the d_count_kept items left
+            const int drop = d_count_kept && shift == 0;
+            const uint32_t *cnt = d_count_kept && shift > 0 ? d_count_kept : d_count;
+            k_upsweep<<<kSortGrid, kThreads, 0, st>>>(kin, cnt, max_n, shift, drop, tmp_hist);
             k_scan_digits<<<kRadix / 8, 256, 0, st>>>(tmp_hist, kSortGrid, dtot);
-            k_downsweep<<<kSortGrid, kThreads, 0, st>>>(kin, vin, kout, vout, d_count, max_n, shift,
-                                                        tmp_hist, dtot);
+            k_downsweep<<<kSortGrid, kThreads, 0, st>>>(kin, vin, kout, vout, cnt, max_n, shift,
+                                                        drop, tmp_hist, dtot);
             uint32_t *t = kin;
             kin = kout;
             kout = t;
@@ -421,12 +435,14 @@ cudaError_t launch_emit(const uint32_t *sorted_pair_ids, int64_t n_pairs_total,
 cudaError_t launch_ranges(const uint32_t *tile_keys, const uint32_t *tile_vals,
                           const PairRec *recs, const TileInfo *tiles, int tile_h, int tile_w,
                           const uint32_t *d_count, int64_t max_pairs, uint2 *ranges,
-                          int64_t n_tiles, uint32_t *entry_rect, cudaStream_t st)
+                          int64_t n_tiles, uint32_t *entry_rect, uint8_t *entry_blocks,
+                          cudaStream_t st)
 {
     cudaError_t e = cudaMemsetAsync(ranges, 0, sizeof(uint2) * static_cast<size_t>(n_tiles), st);
     if (e != cudaSuccess) return e;
     k_ranges<<<4 * kSortGrid, 256, 0, st>>>(tile_keys, tile_vals, recs, tiles, tile_h, tile_w,
-                                            d_count, max_pairs, ranges, entry_rect);
+                                            d_count, max_pairs, ranges, entry_rect,
+                                            entry_blocks);
     return cudaGetLastError();
 }
 
