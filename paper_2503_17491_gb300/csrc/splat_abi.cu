@@ -455,6 +455,7 @@ SPLAT_API int splat_set_views(splat_ctx *ctx, int32_t n_views, const double *T_w
         const double dth = (emax - emin) / (in.rows - 1);
         vd.dgamma = static_cast<float>(2.0 * M_PI / in.cols);
         vd.dtheta = static_cast<float>(dth);
+        splat::set_cull_cones(vd, emin, emax, dth);
         vd.tiles_r = (in.rows + th - 1) / th;
         vd.tiles_c = (in.cols + tw - 1) / tw;
         vd.tile_offset = tiles;

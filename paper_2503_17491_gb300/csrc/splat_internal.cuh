@@ -1,6 +1,7 @@
 // Internal definitions shared by the translation units of libsplatloam (not part of the ABI).
 #pragma once
 
+#include <cmath>
 #include <cstdint>
 #include <cuda_runtime.h>
 
@@ -28,7 +29,25 @@ struct ViewDesc {
     int64_t pixel_offset;         // first pixel of the view in the packed buffers
     int32_t table_offset;         // into the frame table: tiles_r rows then tiles_c columns
     int32_t pix_offset;           // into the pixel-frame table: tiles_r x 256 entries
+    // cones two rows (and a milliradian) beyond the top and bottom rows: z = t |xy|, with
+    // l = sqrt(1 + t^2) the Lipschitz constant of z - t |xy| (l = inf: no cone)
+    float cull_t_top, cull_l_top, cull_t_bot, cull_l_bot;
 };
+
+// the culling cones of a view (host)
+inline void set_cull_cones(ViewDesc &vd, double emin, double emax, double dtheta)
+{
+    const double m = 2.0 * dtheta + 1e-3;
+    const double top = emax + m, bot = emin - m, lim = 1.5;   // well inside +-pi/2
+    vd.cull_t_top = top < lim ? static_cast<float>(std::tan(top)) : 0.0f;
+    vd.cull_l_top = top < lim ? static_cast<float>(std::sqrt(1.0 + std::tan(top) * std::tan(top)) *
+                                                   1.0001)
+                              : INFINITY;
+    vd.cull_t_bot = bot > -lim ? static_cast<float>(std::tan(bot)) : 0.0f;
+    vd.cull_l_bot = bot > -lim ? static_cast<float>(std::sqrt(1.0 + std::tan(bot) * std::tan(bot)) *
+                                                    1.0001)
+                               : INFINITY;
+}
 
 // Frame table entry (float pairs of FP64 sin / cos): per tile row sin/cos of the reference
 // elevation theta0, per tile column sin/cos of the reference azimuth gamma0.
@@ -214,7 +233,7 @@ cudaError_t launch_project(const float4 *pos_logit, const float4 *quat, const fl
 // stable LSD radix sort of (uint32 key, uint32 value) pairs on key bits [0, bits);
 // the count is read on the device from *d_count (clamped to max_n); result lands in
 // (keys_out, vals_out).  tmp_hist holds kHistWords uint32.
-constexpr int kSortGrid = 304;
+constexpr int kSortGrid = 608;    // 4 CTAs per SM (152 SMs)
 constexpr int kSortTile = 2048;   // keys per CTA tile (256 threads x 8)
 constexpr int kHistWords = kSortGrid * 256 + 256;   // per-CTA digit counts + digit totals
 // With d_count_kept non-null the first pass also drops every item whose key is 0xFFFFFFFF (which
@@ -226,7 +245,7 @@ cudaError_t radix_sort_pairs(uint32_t *keys, uint32_t *vals, uint32_t *keys_alt,
                              const uint32_t *d_count_kept = nullptr);
 
 // offsets of every sorted pair, emission of (global tile, pair id) entries, total pair count
-constexpr int kScanGrid = 304;
+constexpr int kScanGrid = 1024;   // the CTA-sum scan runs in one CTA of 1024 threads
 // n_valid: device count of the leading sorted pairs that touch a tile (the rest touch none)
 cudaError_t launch_emit(const uint32_t *sorted_pair_ids, int64_t n_pairs_total,
                         const uint32_t *n_valid, const PairRec *recs, const ViewDesc *views,

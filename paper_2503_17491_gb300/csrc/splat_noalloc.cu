@@ -131,6 +131,7 @@ int build_tables(const double *T, const splat_lidar_intrinsics &in, int th, int 
     const double dth = (emax - emin) / (in.rows - 1);
     vd.dgamma = static_cast<float>(2.0 * M_PI / in.cols);
     vd.dtheta = static_cast<float>(dth);
+    splat::set_cull_cones(vd, emin, emax, dth);
     vd.tiles_r = tiles_r;
     vd.tiles_c = tiles_c;
     vd.tile_offset = 0;

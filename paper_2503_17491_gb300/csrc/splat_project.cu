@@ -320,8 +320,19 @@ __global__ void __launch_bounds__(256) k_project(
             const float dot = (nr.x * bc.x + nr.y * bc.y) + nr.z * bc.z;
             if (flip_normals && dot > 0.0f) rec.cf |= kPairFlip;
             rec.kappa = sqrtf((bc.x * bc.x + bc.y * bc.y) + bc.z * bc.z);
+            // A pair whose whole 3-sigma box lies beyond the view's culling cones (two rows past
+            // the top or bottom row) and away from the z axis reaches no row: every point of
+            // the box is within R = sigma (s_a + s_b) of b_c, and z - t |xy| changes by at most
+            // l R over that ball; staying clear of the axis also keeps the polygon's pole tests
+            // false.  This skips the polygon for such pairs and changes no result.
+            const float rxy = sqrtf(bc.x * bc.x + bc.y * bc.y);
+            const float reach = sigma * (sa + sb) * 1.01f;
+            const bool clear = rxy * 0.99f - reach > 1e-3f;
+            const bool above = bc.z - vd.cull_t_top * rxy > reach * vd.cull_l_top;
+            const bool below = vd.cull_t_bot * rxy - bc.z > reach * vd.cull_l_bot;
             // C4: bounding box
-            rec.cf |= contract_bbox(ba, bb, bc, oc, alpha_min, sigma, vd, tile_h, tile_w, rec);
+            if (!(clear && (above || below)))
+                rec.cf |= contract_bbox(ba, bb, bc, oc, alpha_min, sigma, vd, tile_h, tile_w, rec);
         }
         recs[p] = rec;
         dkeys[p] = (rec.cf & kCountMask) ? __float_as_uint(rec.kappa) : 0xFFFFFFFFu;
