@@ -11,10 +11,14 @@ Parity status per function (what pins it is in ``tests/test_oracle_*.py``):
   render / render_backward : pinned (closed form, invariants, finite differences, brute force)
   project_contract / bin   : pinned (brute-force coverage, wrap/pole/behind cases, series bounds)
   loss / adam              : pinned (hand-computed values, textbook Adam recurrence)
+  render_backward g_pose   : pinned (finite differences of the pose through exp(xi^))
+  backproject              : pinned (round trip through a rendered head-on splat, a wall at a
+                             known distance, pose composition)
 """
 from __future__ import annotations
 
 import ctypes
+import math
 import os
 import subprocess
 import threading
@@ -331,3 +335,32 @@ def full_view(pos_logit, quat, log_scale, T_ws, rows, cols, elev_min, elev_max, 
         out["order"] = order
     out["proj"], out["params"] = proj, params
     return out
+
+
+def pixel_rays(rows, cols, elev_min, elev_max):
+    """Unit ray of every pixel (rows, cols, 3), sensor frame, FP64: column c at azimuth
+    pi - 2 pi (c + 1/2) / W, row r at elevation elev_max - r (elev_max - elev_min) / (H - 1)
+    (elev_max for H = 1) -- the pixel centres of the spherical projection (Sec. 3.1)."""
+    g = math.pi - 2.0 * math.pi * (np.arange(cols) + 0.5) / cols
+    if rows > 1:
+        th = elev_max - np.arange(rows) * (elev_max - elev_min) / (rows - 1)
+    else:
+        th = np.array([elev_max])
+    ct, st = np.cos(th)[:, None], np.sin(th)[:, None]
+    return np.stack([ct * np.cos(g)[None, :], ct * np.sin(g)[None, :],
+                     np.broadcast_to(st, (rows, cols))], 2)
+
+
+def backproject(D, O, T_ws, rows, cols, elev_min, elev_max, o_min):
+    """Back-projection of a rendered range image to a world-frame point cloud (Sec. 3.3: the
+    rasterised range image is back-projected at its pose, p = T_ws phi^-1(u, d)).  D is the
+    unnormalised blended range, so the range of a pixel is d = D / O where O >= o_min (both in
+    binary32, as rendered); other pixels give NaN.  Returns (3, rows * cols) FP64."""
+    D = np.asarray(D, np.float32).reshape(rows, cols)
+    O = np.asarray(O, np.float32).reshape(rows, cols)
+    valid = O >= np.float32(o_min)
+    d = np.where(valid, D.astype(np.float64) / np.where(valid, O, 1).astype(np.float64), np.nan)
+    ps = pixel_rays(rows, cols, elev_min, elev_max) * d[..., None]
+    T = np.asarray(T_ws, np.float64)
+    pw = ps.reshape(-1, 3) @ T[:3, :3].T + T[:3, 3]
+    return pw.T.copy()
