@@ -280,3 +280,36 @@ def test_pose_gradient_batched_views():
     ctx.backward(pl, q, ls, f(gD), f(gN), f(gO))
     with pytest.raises(api._lib.SplatError):
         ctx.pose_gradients()
+
+
+def test_record_pool_overflow_sets_capacity_status():
+    """Faint, wide splats make every 4x8 block record every primitive; with the pair capacity
+    just above the pairs used and the tile capacity at the tiles used, the contributor-record
+    pool runs out: the capacity status bit is set, nothing faults, and the backward still
+    returns finite values.  The same scene with a generous capacity records everything."""
+    rng = np.random.default_rng(12)
+    n = 300
+    g = rng.uniform(-1.2, 1.2, n)
+    r = rng.uniform(3.0, 6.0, n)
+    p = np.stack([r * np.cos(g), r * np.sin(g), rng.uniform(-0.3, 0.3, n)], 1)
+    pl, q, ls = scenes.gaussians_on(p, -p, rng, log_scale=(0.4, 0.5))
+    pl[:, 3] = math.log(0.02 / 0.98)
+    view = scenes.View(np.eye(4), 32, 128, scenes.deg(-20), scenes.deg(20))
+    s = scenes.Scene("faint", pl, q, ls, [view])
+    pl_d, q_d, ls_d = to_dev(s)
+    big = make_ctx(s.n, s.views)
+    big.render(pl_d, q_d, ls_d)
+    assert big.status() == 0
+    st = big.stats()
+    cfg = api.RenderConfig(tile_h=16, tile_w=16)
+    ctx = api.SplatContext(s.n, 1, view.n_pixels, st["n_pairs"] + 8, cfg, max_tiles=st["n_tiles"])
+    ctx.set_views(s.views)
+    d, nrm, a = ctx.render(pl_d, q_d, ls_d)
+    torch.cuda.synchronize()
+    assert ctx.stats()["n_pairs"] == st["n_pairs"]          # the lists themselves fit
+    assert ctx.status() & api._lib.SPLAT_STATUS_CAPACITY     # the records did not
+    P = view.n_pixels
+    g_out = ctx.backward(pl_d, q_d, ls_d, torch.ones(P, device="cuda"),
+                         torch.zeros(3, P, device="cuda"), torch.zeros(P, device="cuda"))
+    torch.cuda.synchronize()
+    assert all(torch.isfinite(t).all() for t in g_out)
