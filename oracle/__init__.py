@@ -14,6 +14,8 @@ Parity status per function (what pins it is in ``tests/test_oracle_*.py``):
   render_backward g_pose   : pinned (finite differences of the pose through exp(xi^))
   backproject              : pinned (round trip through a rendered head-on splat, a wall at a
                              known distance, pose composition)
+  sample_active_views      : pinned (frequencies of the truncated geometric law; Philox words
+                             by uniformity and avalanche, no published output vectors used)
 """
 from __future__ import annotations
 
@@ -364,3 +366,64 @@ def backproject(D, O, T_ws, rows, cols, elev_min, elev_max, o_min):
     T = np.asarray(T_ws, np.float64)
     pw = ps.reshape(-1, 3) @ T[:3, :3].T + T[:3, 3]
     return pw.T.copy()
+
+
+# ---- keyframe sampling (Sec. 3.3, local model refinement) --------------------------------------
+
+_PHILOX_M0, _PHILOX_M1 = 0xD2511F53, 0xCD9E8D57
+_PHILOX_W0, _PHILOX_W1 = 0x9E3779B9, 0xBB67AE85
+_U32 = 0xFFFFFFFF
+
+
+def philox4x32_10(ctr, key):
+    """Philox-4x32 with 10 rounds (Salmon, Moraes, Dror, Shaw, "Parallel random numbers: as easy
+    as 1, 2, 3", SC 2011), written from its definition: a round maps (c0, c1, c2, c3) to
+    (hi(M1 c2) ^ c1 ^ k0, lo(M1 c2), hi(M0 c0) ^ c3 ^ k1, lo(M0 c0)) and the key is bumped by the
+    Weyl constants (W0, W1) between rounds.  Python integers, so no width tricks are involved."""
+    c0, c1, c2, c3 = (int(x) & _U32 for x in ctr)
+    k0, k1 = (int(x) & _U32 for x in key)
+    for r in range(10):
+        p0 = _PHILOX_M0 * c0
+        p1 = _PHILOX_M1 * c2
+        c0, c1, c2, c3 = ((p1 >> 32) ^ c1 ^ k0) & _U32, p1 & _U32, ((p0 >> 32) ^ c3 ^ k1) & _U32, \
+            p0 & _U32
+        if r < 9:
+            k0 = (k0 + _PHILOX_W0) & _U32
+            k1 = (k1 + _PHILOX_W1) & _U32
+    return c0, c1, c2, c3
+
+
+def view_sampling_thresholds(n_views, p_newest):
+    """Integer thresholds of the truncated geometric distribution over keyframe age a
+    (a = 0 the newest): P(a) = p (1 - p)^a / Z over a < n_views, so P(newest) = p / Z >= p.
+    t_a = floor(C_a 2^32) for the cumulative C_a, a < n_views - 1; FP64 with the products and
+    sums taken in age order."""
+    q = 1.0 - p_newest
+    P = []
+    w = p_newest
+    for _ in range(n_views):
+        P.append(w)
+        w = w * q
+    Z = 0.0
+    for x in P:
+        Z = Z + x
+    thr = []
+    c = 0.0
+    for a in range(n_views - 1):
+        c = c + P[a]
+        thr.append(min(int(math.floor((c / Z) * 4294967296.0)), _U32))
+    return thr
+
+
+def sample_active_views(n_views, draws, p_newest, seed, step):
+    """Views drawn for refinement step `step`: draw j in [0, draws) takes the first word x of
+    Philox((j, step, 0, 0), (seed lo, seed hi)), its age is the number of thresholds <= x, and
+    the view is n_views - 1 - age (the last registered view is the newest).  Returns the active
+    flags (a view drawn at least once)."""
+    thr = view_sampling_thresholds(n_views, p_newest)
+    act = np.zeros(n_views, bool)
+    for j in range(draws):
+        x = philox4x32_10((j, step, 0, 0), (seed & _U32, (seed >> 32) & _U32))[0]
+        age = sum(1 for t in thr if x >= t)
+        act[n_views - 1 - age] = True
+    return act
