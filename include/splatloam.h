@@ -212,6 +212,16 @@ SPLAT_API int splat_render_backward(splat_ctx *ctx, const splat_gaussians *g,
 SPLAT_API int splat_set_pose_gradient(splat_ctx *ctx, int enable);
 SPLAT_API int splat_pose_gradient(splat_ctx *ctx, float *g_pose, void *stream);
 
+/* Back-projection of rendered range images to a point cloud (Sec. 3.3: the local model is sampled
+ * by back-projecting the rasterised range image at its estimated pose, p = T_ws phi^-1(u, d)).
+ * depth and alpha: packed images of the context's registered views (as rendered); D is the
+ * unnormalised blend, so a pixel's range is d = D / O, taken where O >= o_min (o_min > 0).
+ * Writes points (device, caller-owned, 3 x P planar, world frame) from the pixel-centre ray of
+ * the spherical projection and the view's pose; NaN where O < o_min.  Stream-ordered.
+ * Errors: INVALID_ARG (null, o_min <= 0), STATE (no views), CUDA. */
+SPLAT_API int splat_backproject(splat_ctx *ctx, const float *depth, const float *alpha,
+                                float o_min, float *points, void *stream);
+
 /* ---- loss and optimiser ------------------------------------------------------------------- */
 
 /* Per-pixel loss over n_pixels packed pixels (depth/alpha/target_depth [P], normal and

@@ -82,6 +82,7 @@ SIGNATURES = {
     "splat_adam_step": ([_P] * 13 + [_I64, ctypes.POINTER(splat_adam_config), _P], _I),
     "splat_refine_step": ([_P, _P, _P, _P, _I64, _P, _P, ctypes.POINTER(splat_loss_config),
                            ctypes.POINTER(splat_adam_config)] + [_P] * 9, _I),
+    "splat_backproject": ([_P, _P, _P, ctypes.c_float, _P, _P], _I),
     "splat_set_pose_gradient": ([_P, _I], _I),
     "splat_pose_gradient": ([_P, _P, _P], _I),
     "splat_get_status": ([_P, ctypes.POINTER(ctypes.c_uint32)], _I),

@@ -202,6 +202,16 @@ class SplatContext:
             _ptr(loss_out), _stream(stream)), "splat_refine_step")
 
     # ---- inspection ---------------------------------------------------------------------
+    def backproject(self, depth, alpha, o_min=0.5, stream=None) -> torch.Tensor:
+        """World-frame points (3, P) of the packed range images (splat_backproject); NaN where
+        alpha < o_min."""
+        _f32(depth, ())
+        _f32(alpha, ())
+        out = torch.empty(3, self.n_pixels, dtype=torch.float32, device=depth.device)
+        _lib.check(self.lib.splat_backproject(self.h, _ptr(depth), _ptr(alpha), float(o_min),
+                                              _ptr(out), _stream(stream)), "splat_backproject")
+        return out
+
     def set_pose_gradient(self, on: bool):
         """Make the following backward calls also form the per-view pose gradient."""
         _lib.check(self.lib.splat_set_pose_gradient(self.h, 1 if on else 0),

@@ -630,6 +630,17 @@ SPLAT_API int splat_render_backward(splat_ctx *ctx, const splat_gaussians *g,
                                        g_quat, g_log_scale, accumulate, stream);
 }
 
+SPLAT_API int splat_backproject(splat_ctx *ctx, const float *depth, const float *alpha,
+                                float o_min, float *points, void *stream)
+{
+    if (!ctx || !depth || !alpha || !points || !(o_min > 0.0f)) return SPLAT_ERR_INVALID_ARG;
+    if (ctx->n_views < 1) return SPLAT_ERR_STATE;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    CK(splat::launch_backproject(ctx->d_views, ctx->n_views, ctx->n_pixels, depth, alpha, o_min,
+                                 points, st));
+    return SPLAT_OK;
+}
+
 SPLAT_API int splat_loss(const float *depth, const float *normal, const float *alpha,
                          const float *target_depth, const float *target_normal,
                          int64_t n_pixels, const splat_loss_config *cfg, float *dL_ddepth,

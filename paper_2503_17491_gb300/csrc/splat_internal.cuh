@@ -34,6 +34,12 @@ struct ViewDesc {
     float cull_t_top, cull_l_top, cull_t_bot, cull_l_bot;
 };
 
+// Back-projection of the packed range images of the registered views to world-frame points
+// (3 x n_pixels planar, NaN where O < o_min).
+cudaError_t launch_backproject(const ViewDesc *views, int n_views, int64_t n_pixels,
+                               const float *depth, const float *alpha, float o_min, float *points,
+                               cudaStream_t st);
+
 // the culling cones of a view (host)
 inline void set_cull_cones(ViewDesc &vd, double emin, double emax, double dtheta)
 {

@@ -174,4 +174,58 @@ cudaError_t launch_step_inc(int32_t *step, cudaStream_t st)
     return cudaGetLastError();
 }
 
+
+// ---------------------------------------------------------------------------------------------
+// back-projection of a rendered range image (Sec. 3.3)
+// ---------------------------------------------------------------------------------------------
+namespace {
+
+// one packed pixel per thread: its view (a scan of the per-view pixel offsets), its ray at the
+// pixel centre, the range D / O where O >= o_min, and the point in the world frame
+// R^c_w^T (p - t^c_w); NaN where invalid
+__global__ void k_backproject(const ViewDesc *__restrict__ views, int n_views, int64_t n_pixels,
+                              const float *__restrict__ depth, const float *__restrict__ alpha,
+                              float o_min, float *__restrict__ points)
+{
+    const int64_t k = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (k >= n_pixels) return;
+    int v = 0;
+    while (v + 1 < n_views && views[v + 1].pixel_offset <= k) ++v;
+    const ViewDesc &vd = views[v];
+    const int64_t local = k - vd.pixel_offset;
+    const int r = static_cast<int>(local / vd.cols), c = static_cast<int>(local % vd.cols);
+    const float O = alpha[k];
+    float px = __int_as_float(0x7FC00000), py = px, pz = px;
+    if (O >= o_min) {
+        const float d = depth[k] / O;
+        const float g = 3.14159265358979f - vd.dgamma * (static_cast<float>(c) + 0.5f);
+        const float th = vd.rows > 1 ? vd.elev_max - vd.dtheta * static_cast<float>(r)
+                                     : vd.elev_max;
+        float sg, cg, st, ct;
+        sincosf(g, &sg, &cg);
+        sincosf(th, &st, &ct);
+        const float sx = d * ct * cg - vd.t_hi[0], sy = d * ct * sg - vd.t_hi[1],
+                    sz = d * st - vd.t_hi[2];
+        const float *R = vd.R_hi;
+        px = R[0] * sx + R[3] * sy + R[6] * sz;
+        py = R[1] * sx + R[4] * sy + R[7] * sz;
+        pz = R[2] * sx + R[5] * sy + R[8] * sz;
+    }
+    points[k] = px;
+    points[n_pixels + k] = py;
+    points[2 * n_pixels + k] = pz;
+}
+
+}  // namespace
+
+cudaError_t launch_backproject(const ViewDesc *views, int n_views, int64_t n_pixels,
+                               const float *depth, const float *alpha, float o_min, float *points,
+                               cudaStream_t st)
+{
+    if (n_pixels <= 0) return cudaSuccess;
+    k_backproject<<<static_cast<unsigned>((n_pixels + 255) / 256), 256, 0, st>>>(
+        views, n_views, n_pixels, depth, alpha, o_min, points);
+    return cudaGetLastError();
+}
+
 }  // namespace splat
