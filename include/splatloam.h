@@ -212,6 +212,23 @@ SPLAT_API int splat_render_backward(splat_ctx *ctx, const splat_gaussians *g,
 SPLAT_API int splat_set_pose_gradient(splat_ctx *ctx, int enable);
 SPLAT_API int splat_pose_gradient(splat_ctx *ctx, float *g_pose, void *stream);
 
+/* Keyframe sampling for refinement (Sec. 3.3: a geometric-distribution scheme that selects the
+ * most recent keyframe with probability at least 40 % and older ones progressively less often).
+ * With draws > 0, every following render (splat_render_views, splat_refine_step) first draws
+ * `draws` keyframes on the device from P(age a) = p (1 - p)^a / Z over the registered views (age
+ * 0 = the last registered view; p = p_newest, so P(newest) >= p): draw j of call s takes the
+ * first word x of Philox-4x32-10 (counter (j, s, 0, 0), key (seed low, seed high)) and its age is
+ * the number of thresholds floor(C_a 2^32) (C the FP64 cumulative law, a < n_views - 1) at or
+ * below x.  Views not drawn take no primitives in that call (their images are zero) and their
+ * pixels do not enter splat_refine_step's loss.  The call counter s restarts at 0 here;
+ * splat_set_views turns sampling off.  draws = 0 turns it off.
+ * Errors: INVALID_ARG (draws < 0, p_newest outside (0, 1]), STATE (no views), CUDA. */
+SPLAT_API int splat_set_view_sampling(splat_ctx *ctx, int draws, double p_newest, uint64_t seed);
+
+/* The views drawn for the last render (1 = drawn), n_views bytes to host memory (synchronising);
+ * all ones when sampling is off.  Errors: INVALID_ARG, STATE (no views), CUDA. */
+SPLAT_API int splat_get_active_views(splat_ctx *ctx, uint8_t *flags);
+
 /* Back-projection of rendered range images to a point cloud (Sec. 3.3: the local model is sampled
  * by back-projecting the rasterised range image at its estimated pose, p = T_ws phi^-1(u, d)).
  * depth and alpha: packed images of the context's registered views (as rendered); D is the

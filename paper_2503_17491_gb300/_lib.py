@@ -83,6 +83,8 @@ SIGNATURES = {
     "splat_refine_step": ([_P, _P, _P, _P, _I64, _P, _P, ctypes.POINTER(splat_loss_config),
                            ctypes.POINTER(splat_adam_config)] + [_P] * 9, _I),
     "splat_backproject": ([_P, _P, _P, ctypes.c_float, _P, _P], _I),
+    "splat_set_view_sampling": ([_P, _I, ctypes.c_double, ctypes.c_uint64], _I),
+    "splat_get_active_views": ([_P, _P], _I),
     "splat_set_pose_gradient": ([_P, _I], _I),
     "splat_pose_gradient": ([_P, _P, _P], _I),
     "splat_get_status": ([_P, ctypes.POINTER(ctypes.c_uint32)], _I),

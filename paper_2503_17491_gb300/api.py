@@ -202,6 +202,18 @@ class SplatContext:
             _ptr(loss_out), _stream(stream)), "splat_refine_step")
 
     # ---- inspection ---------------------------------------------------------------------
+    def set_view_sampling(self, draws: int, p_newest: float = 0.4, seed: int = 0):
+        """Draw `draws` keyframes per render from the truncated geometric law over keyframe age
+        (splat_set_view_sampling); draws = 0 renders every view."""
+        _lib.check(self.lib.splat_set_view_sampling(self.h, int(draws), float(p_newest),
+                                                    int(seed)), "splat_set_view_sampling")
+
+    def active_views(self) -> np.ndarray:
+        flags = np.zeros(len(self.views), np.uint8)
+        _lib.check(self.lib.splat_get_active_views(self.h, flags.ctypes.data_as(_P)),
+                   "splat_get_active_views")
+        return flags.astype(bool)
+
     def backproject(self, depth, alpha, o_min=0.5, stream=None) -> torch.Tensor:
         """World-frame points (3, P) of the packed range images (splat_backproject); NaN where
         alpha < o_min."""

@@ -100,7 +100,7 @@ struct splat_ctx {
     float *d_gimg = nullptr;    // refine: their gradients
     uint32_t *d_counters = nullptr;   // [0] pairs M, [1] status, [2] queue f, [3] queue b,
                                       // [4] (view, primitive) pairs that touch a tile,
-                                      // [5] record chunks taken
+                                      // [5] record chunks taken, [7] sampling step
     unsigned long long *d_evals = nullptr;      // [0] forward, [1] backward
 
     // profiling events around the compositing kernels: [0,1] forward, [2,3] backward
@@ -112,6 +112,10 @@ struct splat_ctx {
     // state of the last render
     bool rendered = false;
     bool have_pose = false;         // a backward with pose terms ran since the views were set
+    int samp_draws = 0;             // keyframe sampling: draws per step (0 = every view)
+    uint64_t samp_seed = 0;
+    uint32_t *d_samp_thr = nullptr;   // integer thresholds of the sampling law
+    uint8_t *d_active = nullptr;      // per view: sampled for the current step
     bool want_pose = false;         // backward calls also accumulate the pose gradient
     int64_t last_n = 0;
     uint32_t *sorted_keys = nullptr, *sorted_vals = nullptr;
@@ -184,12 +188,21 @@ int render_core(splat_ctx *ctx, const splat_gaussians *g, float *depth, float *n
     CK(cudaMemsetAsync(cnt + 4, 0, 2 * sizeof(uint32_t), st));   // touching pairs, chunks
     CK(cudaMemsetAsync(cnt + 2, 0, sizeof(uint32_t), st));       // forward queue
     CK(cudaMemsetAsync(ctx->d_evals, 0, sizeof(unsigned long long), st));
+    const uint8_t *active = nullptr;
+    if (ctx->samp_draws > 0) {
+        CK(splat::launch_sample_views(ctx->n_views, ctx->samp_draws, ctx->d_samp_thr,
+                                      static_cast<uint32_t>(ctx->samp_seed),
+                                      static_cast<uint32_t>(ctx->samp_seed >> 32), cnt + 7,
+                                      ctx->d_active, st));
+        active = ctx->d_active;
+    }
     CK(splat::launch_project(reinterpret_cast<const float4 *>(g->pos_logit),
                              reinterpret_cast<const float4 *>(g->quat_wxyz),
                              reinterpret_cast<const float2 *>(g->log_scale), n, ctx->d_views,
                              ctx->n_views, ctx->cfg.sigma_cut, ctx->cfg.alpha_min, th, tw,
                              ctx->cfg.flip_normals,
-                             ctx->d_recs, ctx->d_dkeys, ctx->d_dvals, cnt + 1, cnt + 4, st));
+                             ctx->d_recs, ctx->d_dkeys, ctx->d_dvals, cnt + 1, cnt + 4, st,
+                             active));
     uint32_t *dk, *dv;
     // the range sort drops the pairs that touch no tile (key 0xFFFFFFFF) in its first pass
     CK(splat::radix_sort_pairs(ctx->d_dkeys, ctx->d_dvals, ctx->d_dkeys2, ctx->d_dvals2, nullptr,
@@ -269,6 +282,7 @@ void free_ctx(splat_ctx *c)
                     c->d_dkeys2, c->d_dvals2, c->d_tkeys, c->d_tvals, c->d_tkeys2, c->d_tvals2,
                     c->d_block_sums, c->d_hist, c->d_ranges, c->d_tfinal, c->d_nlast, c->d_wgrad,
                     c->d_pose, c->d_rec, c->d_rec_prev, c->d_rec_head, c->d_rec_fill,
+                    c->d_samp_thr, c->d_active,
                     c->d_img, c->d_gimg, c->d_counters, c->d_evals, c->d_pixframes,
                     c->d_tileinfo, c->d_tile_order};
     for (void *p : ptrs)
@@ -364,6 +378,8 @@ SPLAT_API int splat_ctx_create(const splat_render_config *cfg, const splat_capac
     if (e == cudaSuccess) e = dalloc(&c->d_nlast, P);
     if (e == cudaSuccess) e = dalloc(&c->d_wgrad, static_cast<size_t>(cap->max_gaussians) * 4);
     if (e == cudaSuccess) e = dalloc(&c->d_pose, static_cast<size_t>(cap->max_views) * 6);
+    if (e == cudaSuccess) e = dalloc(&c->d_samp_thr, static_cast<size_t>(splat::kMaxViews));
+    if (e == cudaSuccess) e = dalloc(&c->d_active, static_cast<size_t>(cap->max_views));
     // contributor records: at most one per (block, staged entry); the pool takes two per
     // (tile, primitive) pair of capacity plus one partial chunk per work item
     const int64_t items = TT * (splat::kBlock / 32);
@@ -568,6 +584,7 @@ SPLAT_API int splat_set_views(splat_ctx *ctx, int32_t n_views, const double *T_w
     ctx->n_tiles = tiles;
     ctx->rendered = false;
     ctx->have_pose = false;
+    ctx->samp_draws = 0;   // the sampling law depends on the views: set it again
     return SPLAT_OK;
 }
 
@@ -716,7 +733,9 @@ SPLAT_API int splat_refine_step(splat_ctx *ctx, float *pos_logit, float *quat, f
     if (r) return r;
     CK(cudaMemsetAsync(loss_out, 0, sizeof(double), st));
     CK(splat::launch_loss(depth, normal, alpha, target_depth, target_normal, P, loss_cfg->lambda_n,
-                          loss_cfg->lambda_o, loss_cfg->o_eps, gd, gn, ga, loss_out, st));
+                          loss_cfg->lambda_o, loss_cfg->o_eps, gd, gn, ga, loss_out, st,
+                          ctx->d_views, ctx->n_views,
+                          ctx->samp_draws > 0 ? ctx->d_active : nullptr));
     r = backward_core(ctx, &g, gd, gn, ga, st);
     if (r) return r;
     splat::AdamArgs a{};
@@ -741,6 +760,55 @@ SPLAT_API int splat_refine_step(splat_ctx *ctx, float *pos_logit, float *quat, f
     CK(splat::launch_adam_fused(a, ctx->d_wgrad, st));
     CK(splat::launch_step_inc(step, st));
     ctx->launches += 3;   // loss, fused Adam, step counter
+    return SPLAT_OK;
+}
+
+SPLAT_API int splat_set_view_sampling(splat_ctx *ctx, int draws, double p_newest, uint64_t seed)
+{
+    if (!ctx || draws < 0) return SPLAT_ERR_INVALID_ARG;
+    if (draws == 0) {
+        ctx->samp_draws = 0;
+        return SPLAT_OK;
+    }
+    if (!(p_newest > 0.0 && p_newest <= 1.0)) return SPLAT_ERR_INVALID_ARG;
+    if (ctx->n_views < 1) return SPLAT_ERR_STATE;
+    // truncated geometric law over keyframe age, cumulative, as integer thresholds (FP64, the
+    // products and sums in age order)
+    const int K = ctx->n_views;
+    std::vector<double> P(static_cast<size_t>(K));
+    double w = p_newest;
+    for (int a = 0; a < K; ++a) {
+        P[a] = w;
+        w = w * (1.0 - p_newest);
+    }
+    double Z = 0.0;
+    for (int a = 0; a < K; ++a) Z = Z + P[a];
+    std::vector<uint32_t> thr(static_cast<size_t>(splat::kMaxViews), 0u);
+    double c = 0.0;
+    for (int a = 0; a + 1 < K; ++a) {
+        c = c + P[a];
+        const double v = std::floor((c / Z) * 4294967296.0);
+        thr[a] = v >= 4294967295.0 ? 0xFFFFFFFFu : static_cast<uint32_t>(v);
+    }
+    CK(cudaMemcpy(ctx->d_samp_thr, thr.data(), sizeof(uint32_t) * thr.size(),
+                  cudaMemcpyHostToDevice));
+    CK(cudaMemset(ctx->d_counters + 7, 0, sizeof(uint32_t)));
+    ctx->samp_draws = draws;
+    ctx->samp_seed = seed;
+    return SPLAT_OK;
+}
+
+SPLAT_API int splat_get_active_views(splat_ctx *ctx, uint8_t *flags)
+{
+    if (!ctx || !flags) return SPLAT_ERR_INVALID_ARG;
+    if (ctx->n_views < 1) return SPLAT_ERR_STATE;
+    CK(cudaDeviceSynchronize());
+    if (ctx->samp_draws > 0) {
+        CK(cudaMemcpy(flags, ctx->d_active, static_cast<size_t>(ctx->n_views),
+                      cudaMemcpyDeviceToHost));
+    } else {
+        for (int v = 0; v < ctx->n_views; ++v) flags[v] = 1;
+    }
     return SPLAT_OK;
 }
 

@@ -34,6 +34,14 @@ struct ViewDesc {
     float cull_t_top, cull_l_top, cull_t_bot, cull_l_bot;
 };
 
+// Keyframe sampling (Sec. 3.3): draws j < draws of refinement step *step take the first word x of
+// Philox-4x32-10((j, step, 0, 0), (seed lo, seed hi)); the drawn view is n_views - 1 - #{a :
+// x >= thr[a]} (thr: n_views - 1 integer thresholds of the cumulative law); active[v] = 1 for a
+// view drawn at least once, 0 otherwise; *step then advances by one.
+cudaError_t launch_sample_views(int n_views, int draws, const uint32_t *thr, uint32_t seed_lo,
+                                uint32_t seed_hi, uint32_t *step, uint8_t *active,
+                                cudaStream_t st);
+
 // Back-projection of the packed range images of the registered views to world-frame points
 // (3 x n_pixels planar, NaN where O < o_min).
 cudaError_t launch_backproject(const ViewDesc *views, int n_views, int64_t n_pixels,
@@ -234,7 +242,7 @@ cudaError_t launch_project(const float4 *pos_logit, const float4 *quat, const fl
                            int64_t n, const ViewDesc *views, int n_views, float sigma,
                            float alpha_min, int tile_h, int tile_w, int flip_normals,
                            PairRec *recs, uint32_t *dkeys, uint32_t *dvals, uint32_t *status,
-                           uint32_t *n_valid, cudaStream_t st);
+                           uint32_t *n_valid, cudaStream_t st, const uint8_t *active = nullptr);
 
 // stable LSD radix sort of (uint32 key, uint32 value) pairs on key bits [0, bits);
 // the count is read on the device from *d_count (clamped to max_n); result lands in
@@ -376,10 +384,14 @@ cudaError_t launch_param_grads(const float4 *pos_logit, const float4 *quat, cons
                                const float4 *wgrad, int64_t n, float4 *g_pos_logit, float4 *g_quat,
                                float2 *g_log_scale, int accumulate, cudaStream_t st);
 
+// active (nullable): pixels of views with active[v] == 0 count as invalid (views: the registered
+// views, for the pixel -> view lookup)
 cudaError_t launch_loss(const float *depth, const float *normal, const float *alpha,
                         const float *t_depth, const float *t_normal, int64_t n_pixels,
                         float lambda_n, float lambda_o, float o_eps, float *g_depth,
-                        float *g_normal, float *g_alpha, double *loss_out, cudaStream_t st);
+                        float *g_normal, float *g_alpha, double *loss_out, cudaStream_t st,
+                        const ViewDesc *views = nullptr, int n_views = 0,
+                        const uint8_t *active = nullptr);
 
 struct AdamArgs {
     float4 *pos_logit;

@@ -25,7 +25,9 @@ __global__ void __launch_bounds__(256) k_loss(const float *__restrict__ depth,
                                               float *__restrict__ g_depth,
                                               float *__restrict__ g_normal,
                                               float *__restrict__ g_alpha,
-                                              double *__restrict__ loss_out)
+                                              double *__restrict__ loss_out,
+                                              const ViewDesc *__restrict__ views, int n_views,
+                                              const uint8_t *__restrict__ active)
 {
     __shared__ double s_part[8];
     float acc = 0.0f;
@@ -33,7 +35,13 @@ __global__ void __launch_bounds__(256) k_loss(const float *__restrict__ depth,
          p += static_cast<int64_t>(gridDim.x) * blockDim.x) {
         const float dt = t_depth[p];
         float gd = 0.0f, gn0 = 0.0f, gn1 = 0.0f, gn2 = 0.0f, go = 0.0f;
-        if (dt > 0.0f) {
+        bool use = dt > 0.0f;
+        if (active && use) {   // pixels of views not sampled for this step do not count
+            int v = 0;
+            while (v + 1 < n_views && views[v + 1].pixel_offset <= p) ++v;
+            use = active[v] != 0;
+        }
+        if (use) {
             const float e = depth[p] - dt;
             acc += fabsf(e);
             gd = e > 0.0f ? 1.0f : (e < 0.0f ? -1.0f : 0.0f);
@@ -142,14 +150,16 @@ __global__ void k_step_inc(int32_t *step)
 cudaError_t launch_loss(const float *depth, const float *normal, const float *alpha,
                         const float *t_depth, const float *t_normal, int64_t n_pixels,
                         float lambda_n, float lambda_o, float o_eps, float *g_depth,
-                        float *g_normal, float *g_alpha, double *loss_out, cudaStream_t st)
+                        float *g_normal, float *g_alpha, double *loss_out, cudaStream_t st,
+                        const ViewDesc *views, int n_views, const uint8_t *active)
 {
     if (n_pixels <= 0) return cudaSuccess;
     int64_t blocks = (n_pixels + 255) / 256;
     if (blocks > 4096) blocks = 4096;
     k_loss<<<static_cast<unsigned>(blocks), 256, 0, st>>>(depth, normal, alpha, t_depth, t_normal,
                                                           n_pixels, lambda_n, lambda_o, o_eps,
-                                                          g_depth, g_normal, g_alpha, loss_out);
+                                                          g_depth, g_normal, g_alpha, loss_out,
+                                                          views, n_views, active);
     return cudaGetLastError();
 }
 
@@ -225,6 +235,60 @@ cudaError_t launch_backproject(const ViewDesc *views, int n_views, int64_t n_pix
     if (n_pixels <= 0) return cudaSuccess;
     k_backproject<<<static_cast<unsigned>((n_pixels + 255) / 256), 256, 0, st>>>(
         views, n_views, n_pixels, depth, alpha, o_min, points);
+    return cudaGetLastError();
+}
+
+
+// ---------------------------------------------------------------------------------------------
+// keyframe sampling (Sec. 3.3)
+// ---------------------------------------------------------------------------------------------
+namespace {
+
+// Philox-4x32-10 (Salmon, Moraes, Dror, Shaw, SC 2011), from its definition: a round maps
+// (c0, c1, c2, c3) to (hi(M1 c2) ^ c1 ^ k0, lo(M1 c2), hi(M0 c0) ^ c3 ^ k1, lo(M0 c0)); the key
+// is bumped by the Weyl constants between rounds.
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k)
+{
+    constexpr uint32_t M0 = 0xD2511F53u, M1 = 0xCD9E8D57u, W0 = 0x9E3779B9u, W1 = 0xBB67AE85u;
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const uint32_t hi0 = __umulhi(M0, c.x), lo0 = M0 * c.x;
+        const uint32_t hi1 = __umulhi(M1, c.z), lo1 = M1 * c.z;
+        c = make_uint4(hi1 ^ c.y ^ k.x, lo1, hi0 ^ c.w ^ k.y, lo0);
+        if (r < 9) {
+            k.x += W0;
+            k.y += W1;
+        }
+    }
+    return c;
+}
+
+__global__ void k_sample_views(int n_views, int draws, const uint32_t *__restrict__ thr,
+                               uint32_t seed_lo, uint32_t seed_hi, uint32_t *__restrict__ step,
+                               uint8_t *__restrict__ active)
+{
+    const int lane = threadIdx.x;
+    const uint32_t s = *step;
+    for (int v = lane; v < n_views; v += 32) active[v] = 0;
+    __syncwarp();
+    for (int j = lane; j < draws; j += 32) {
+        const uint32_t x = philox4x32_10(make_uint4(static_cast<uint32_t>(j), s, 0u, 0u),
+                                         make_uint2(seed_lo, seed_hi)).x;
+        int age = 0;
+        for (int a = 0; a + 1 < n_views; ++a) age += x >= thr[a] ? 1 : 0;
+        active[n_views - 1 - age] = 1;
+    }
+    __syncwarp();
+    if (lane == 0) *step = s + 1u;
+}
+
+}  // namespace
+
+cudaError_t launch_sample_views(int n_views, int draws, const uint32_t *thr, uint32_t seed_lo,
+                                uint32_t seed_hi, uint32_t *step, uint8_t *active,
+                                cudaStream_t st)
+{
+    k_sample_views<<<1, 32, 0, st>>>(n_views, draws, thr, seed_lo, seed_hi, step, active);
     return cudaGetLastError();
 }
 

@@ -267,7 +267,7 @@ __global__ void __launch_bounds__(256) k_project(
     int n_views, float sigma, float alpha_min, int tile_h, int tile_w, int flip_normals,
     PairRec *__restrict__ recs,
     uint32_t *__restrict__ dkeys, uint32_t *__restrict__ dvals, uint32_t *__restrict__ status,
-    uint32_t *__restrict__ n_valid)
+    uint32_t *__restrict__ n_valid, const uint8_t *__restrict__ active)
 {
     const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
     if (i >= n) return;
@@ -330,8 +330,8 @@ __global__ void __launch_bounds__(256) k_project(
             const bool clear = rxy * 0.99f - reach > 1e-3f;
             const bool above = bc.z - vd.cull_t_top * rxy > reach * vd.cull_l_top;
             const bool below = vd.cull_t_bot * rxy - bc.z > reach * vd.cull_l_bot;
-            // C4: bounding box
-            if (!(clear && (above || below)))
+            // C4: bounding box (views not sampled for this step take no pairs)
+            if (!(clear && (above || below)) && !(active && !active[v]))
                 rec.cf |= contract_bbox(ba, bb, bc, oc, alpha_min, sigma, vd, tile_h, tile_w, rec);
         }
         recs[p] = rec;
@@ -352,13 +352,13 @@ cudaError_t launch_project(const float4 *pos_logit, const float4 *quat, const fl
                            int64_t n, const ViewDesc *views, int n_views, float sigma,
                            float alpha_min, int tile_h, int tile_w, int flip_normals,
                            PairRec *recs, uint32_t *dkeys, uint32_t *dvals, uint32_t *status,
-                           uint32_t *n_valid, cudaStream_t st)
+                           uint32_t *n_valid, cudaStream_t st, const uint8_t *active)
 {
     if (n <= 0) return cudaSuccess;
     const unsigned grid = static_cast<unsigned>((n + 255) / 256);
     k_project<<<grid, 256, 0, st>>>(pos_logit, quat, log_scale, n, views, n_views, sigma,
                                     alpha_min, tile_h, tile_w, flip_normals, recs, dkeys, dvals,
-                                    status, n_valid);
+                                    status, n_valid, active);
     return cudaGetLastError();
 }
 
