@@ -16,6 +16,7 @@ Parity status per function (what pins it is in ``tests/test_oracle_*.py``):
                              known distance, pose composition)
   sample_active_views      : pinned (frequencies of the truncated geometric law; Philox words
                              by uniformity and avalanche, no published output vectors used)
+  scale_regularizer        : pinned (hand values, finite differences)
 """
 from __future__ import annotations
 
@@ -427,3 +428,19 @@ def sample_active_views(n_views, draws, p_newest, seed, step):
         age = sum(1 for t in thr if x >= t)
         act[n_views - 1 - age] = True
     return act
+
+
+def scale_regularizer(log_scale, lambda_s, tau_s):
+    """Scale term of the mapping loss (Eq. L_s, its sign read as a penalty on growth beyond
+    tau_s): lambda_s sum_i max(0, max(s_a, s_b)_i - tau_s), s = exp(log s), and its gradient with
+    respect to log s (s of the larger axis, the first one on a tie).  FP64."""
+    ls = np.asarray(log_scale, np.float64).reshape(-1, 2)
+    s = np.exp(ls)
+    first = s[:, 0] >= s[:, 1]
+    sm = np.where(first, s[:, 0], s[:, 1])
+    on = sm > tau_s
+    value = lambda_s * float(np.sum(np.where(on, sm - tau_s, 0.0)))
+    g = np.zeros_like(ls)
+    g[:, 0] = np.where(on & first, lambda_s * s[:, 0], 0.0)
+    g[:, 1] = np.where(on & ~first, lambda_s * s[:, 1], 0.0)
+    return value, g

@@ -65,3 +65,26 @@ def test_loss_wrapper_with_converted_inputs(oracle_mod):
     assert L == L2
     v = Dt > 0
     assert np.array_equal(gD != 0, v & (D != Dt))
+
+
+def test_scale_regularizer_values_and_gradient(oracle_mod):
+    """Hand values of the scale term and central differences of its gradient away from the
+    threshold and from ties."""
+    import math
+    ls = np.log(np.array([[2.0, 1.0], [0.3, 0.4], [0.5, 3.0], [1.2, 1.2]]))
+    v, g = oracle_mod.scale_regularizer(ls, 0.5, 1.0)
+    assert math.isclose(v, 0.5 * ((2.0 - 1.0) + 0.0 + (3.0 - 1.0) + (1.2 - 1.0)), rel_tol=1e-12)
+    np.testing.assert_allclose(g, [[1.0, 0.0], [0.0, 0.0], [0.0, 1.5], [0.6, 0.0]], rtol=1e-12)
+    rng = np.random.default_rng(4)
+    ls = rng.uniform(-1.5, 1.5, (30, 2))
+    _, g = oracle_mod.scale_regularizer(ls, 0.7, 1.3)
+    for i in range(30):
+        for k in range(2):
+            h = 1e-6
+            a, b = ls.copy(), ls.copy()
+            a[i, k] += h
+            b[i, k] -= h
+            fd = (oracle_mod.scale_regularizer(a, 0.7, 1.3)[0] -
+                  oracle_mod.scale_regularizer(b, 0.7, 1.3)[0]) / (2 * h)
+            if abs(math.exp(ls[i, k]) - 1.3) > 1e-3 and abs(ls[i, 0] - ls[i, 1]) > 1e-3:
+                assert abs(fd - g[i, k]) <= 1e-6 * max(1.0, abs(g[i, k])), (i, k, fd, g[i, k])
