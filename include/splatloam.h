@@ -109,9 +109,12 @@ typedef struct {
     int64_t max_tiles;
 } splat_capacity;
 
-/* Loss weights (Eq. loss_full with rho_d = 1 and lambda_s = 0): o_eps floors O inside -log O. */
+/* Loss weights of Eq. loss_full (rho_d = 1): o_eps floors O inside -log O.  lambda_s and tau_s
+ * weigh the scale term of splat_refine_step, lambda_s sum_i max(0, max(s_a, s_b)_i - tau_s) (the
+ * penalty of Eq. L_s with its sign read as growth beyond tau_s; 0 disables it). */
 typedef struct {
     float lambda_n, lambda_o, o_eps;
+    float lambda_s, tau_s;
 } splat_loss_config;
 
 /* Adam settings; one learning rate per parameter group. */

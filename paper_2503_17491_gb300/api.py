@@ -76,9 +76,12 @@ class LossConfig:
     lambda_n: float = 1.0
     lambda_o: float = 0.0
     o_eps: float = 1e-6
+    lambda_s: float = 0.0   # scale term (splat_refine_step only)
+    tau_s: float = 0.5
 
     def c(self):
-        return _lib.splat_loss_config(self.lambda_n, self.lambda_o, self.o_eps)
+        return _lib.splat_loss_config(self.lambda_n, self.lambda_o, self.o_eps, self.lambda_s,
+                                      self.tau_s)
 
 
 @dataclass

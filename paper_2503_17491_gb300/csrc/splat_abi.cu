@@ -757,6 +757,9 @@ SPLAT_API int splat_refine_step(splat_ctx *ctx, float *pos_logit, float *quat, f
     a.beta1 = adam_cfg->beta1;
     a.beta2 = adam_cfg->beta2;
     a.eps = adam_cfg->eps;
+    a.lambda_s = loss_cfg->lambda_s;
+    a.tau_s = loss_cfg->tau_s;
+    a.loss_out = loss_out;
     CK(splat::launch_adam_fused(a, ctx->d_wgrad, st));
     CK(splat::launch_step_inc(step, st));
     ctx->launches += 3;   // loss, fused Adam, step counter

@@ -404,6 +404,9 @@ struct AdamArgs {
     int32_t *step;
     int64_t n;
     float lr_pos, lr_opacity, lr_rot, lr_scale, beta1, beta2, eps;
+    // scale term (fused form only): lambda_s max(0, max(s_a, s_b) - tau_s), added to *loss_out
+    float lambda_s, tau_s;
+    double *loss_out;
 };
 
 // Adam from explicit parameter gradients

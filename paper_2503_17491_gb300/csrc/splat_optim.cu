@@ -137,6 +137,23 @@ __global__ void __launch_bounds__(256) k_adam_fused(const AdamArgs a,
     float4 gp, gq;
     float2 gl;
     chain_params(a.pos_logit[i], a.quat[i], wgrad + 4 * i, gp, gq, gl);
+    if (a.lambda_s != 0.0f) {
+        // scale term: growth of the larger scale beyond tau_s (the first axis on a tie);
+        // d/dlog s = s
+        const float2 ls = a.log_scale[i];
+        const float sa = expf(ls.x), sb = expf(ls.y);
+        const float sm = fmaxf(sa, sb);
+        float pen = 0.0f;
+        if (sm > a.tau_s) {
+            pen = a.lambda_s * (sm - a.tau_s);
+            if (sa >= sb) gl.x += a.lambda_s * sa;
+            else gl.y += a.lambda_s * sb;
+        }
+        double acc = static_cast<double>(pen);
+        const unsigned am = __activemask();
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(am, acc, o);
+        if ((threadIdx.x & 31) == __ffs(am) - 1 && acc != 0.0) atomicAdd(a.loss_out, acc);
+    }
     adam_prim(a, i, gp, gq, gl, adam_scalars(a));
 }
 

@@ -313,3 +313,33 @@ def test_record_pool_overflow_sets_capacity_status():
                          torch.zeros(3, P, device="cuda"), torch.zeros(P, device="cuda"))
     torch.cuda.synchronize()
     assert all(torch.isfinite(t).all() for t in g_out)
+
+
+def test_refine_step_scale_term():
+    """splat_refine_step with the scale term: the loss grows by the oracle's L_s, and Adam's
+    first moment of the log-scales by (1 - beta1) times the oracle's L_s gradient (one step from
+    zero moments, same render gradients)."""
+    s = scenes.workload(3, n=20_000)
+    views = s.views[:3]
+    targets = [scenes.render_targets(s, v) for v in views]
+    t_depth = torch.from_numpy(np.concatenate([t[0].ravel() for t in targets])).cuda()
+    t_normal = torch.from_numpy(np.concatenate([t[1].reshape(3, -1) for t in targets],
+                                               1)).contiguous().cuda()
+    adam_cfg = api.AdamConfig()
+    out = {}
+    for lam in (0.0, 0.3):
+        params = [t.clone() for t in to_dev(s)]
+        state = api.adam_state(s.n)
+        loss_out = torch.zeros(1, dtype=torch.float64, device="cuda")
+        ctx = make_ctx(s.n, views)
+        ctx.refine_step(params, state, t_depth, t_normal, api.LossConfig(lambda_s=lam, tau_s=0.15),
+                        adam_cfg, loss_out)
+        out[lam] = (float(loss_out.item()), state[2].double().cpu().numpy())
+    v_s, g_s = oracle.scale_regularizer(s.log_scale, 0.3, 0.15)
+    assert v_s > 0 and (g_s != 0).sum() > 1000
+    assert out[0.3][0] - out[0.0][0] == pytest.approx(v_s, rel=1e-5)
+    dm = (out[0.3][1] - out[0.0][1]) / (1.0 - adam_cfg.beta1)
+    g_render = np.abs(out[0.0][1]) / (1.0 - adam_cfg.beta1)
+    # the render gradients are summed with float atomics: the two runs differ by their rounding
+    tol = 1e-4 * g_render + 1e-6
+    assert (np.abs(dm - g_s) <= tol).all(), np.abs(dm - g_s).max()
