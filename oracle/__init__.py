@@ -17,6 +17,8 @@ Parity status per function (what pins it is in ``tests/test_oracle_*.py``):
   sample_active_views      : pinned (frequencies of the truncated geometric law; Philox words
                              by uniformity and avalanche, no published output vectors used)
   scale_regularizer        : pinned (hand values, finite differences)
+  range_normal_loss        : pinned (a planar range map gives the plane's normal; finite
+                             differences in D and N)
 """
 from __future__ import annotations
 
@@ -444,3 +446,48 @@ def scale_regularizer(log_scale, lambda_s, tau_s):
     g[:, 0] = np.where(on & first, lambda_s * s[:, 0], 0.0)
     g[:, 1] = np.where(on & ~first, lambda_s * s[:, 1], 0.0)
     return value, g
+
+
+def range_normal_loss(D, N, Dt, rows, cols, elev_min, elev_max, lambda_n=1.0):
+    """Self-regularised normal term of the mapping loss (Eq. loss_normal): the rendered normal N is
+    compared with the normal of the rendered range map, N(D) (Sec. 3.3, after 2DGS).  Reading:
+    for pixel u = (r, c) with r + 1 < H, x = (r, c + 1 mod W) and y = (r + 1, c) (the azimuth
+    wraps), P(w) = D(w) v(w) with v the pixel-centre ray, m = (P(x) - P(u)) x (P(y) - P(u)),
+    n_D = -sign(m . v(u)) m / |m| (facing the sensor); the term lambda_n (1 - N(u) . n_D) counts
+    where the targets of u, x and y are valid (Dt > 0) and m != 0.  D and N are used as rendered
+    (unnormalised blends).  Returns (value, dL/dD (H, W), dL/dN (3, H, W)), FP64; the sign
+    is held fixed in the gradient."""
+    D = np.asarray(D, np.float64).reshape(rows, cols)
+    N = np.asarray(N, np.float64).reshape(3, rows, cols)
+    Dt = np.asarray(Dt, np.float64).reshape(rows, cols)
+    V = pixel_rays(rows, cols, elev_min, elev_max)
+    P = V * D[..., None]
+    gD = np.zeros((rows, cols))
+    gP = np.zeros((rows, cols, 3))
+    gN = np.zeros((3, rows, cols))
+    value = 0.0
+    for r in range(rows - 1):
+        for c in range(cols):
+            cx = (c + 1) % cols
+            if not (Dt[r, c] > 0 and Dt[r, cx] > 0 and Dt[r + 1, c] > 0):
+                continue
+            dx = P[r, cx] - P[r, c]
+            dy = P[r + 1, c] - P[r, c]
+            m = np.cross(dx, dy)
+            mn = np.linalg.norm(m)
+            if mn == 0.0:
+                continue
+            s = -1.0 if np.dot(m, V[r, c]) > 0 else 1.0
+            nd = s * m / mn
+            n = N[:, r, c]
+            value += lambda_n * (1.0 - np.dot(n, nd))
+            gN[:, r, c] += -lambda_n * nd
+            g = -lambda_n * n                                  # dL/dn_D
+            gm = s * (g - (m / mn) * np.dot(m / mn, g)) / mn     # dL/dm
+            gdx = np.cross(dy, gm)
+            gdy = np.cross(gm, dx)
+            gP[r, cx] += gdx
+            gP[r + 1, c] += gdy
+            gP[r, c] -= gdx + gdy
+    gD = np.einsum("hwk,hwk->hw", gP, V)
+    return value, gD, gN
