@@ -19,6 +19,10 @@ Parity status per function (what pins it is in ``tests/test_oracle_*.py``):
   scale_regularizer        : pinned (hand values, finite differences)
   range_normal_loss        : pinned (a planar range map gives the plane's normal; finite
                              differences in D and N)
+  densify                  : pinned (systematic-sampling counts against brute-force enumeration
+                             of the sample points, evenly spaced picks on flat weights, masks by
+                             their definitions, a step edge's weight, selection frequencies over
+                             many draws; new primitives by round trip through the projection)
 """
 from __future__ import annotations
 
@@ -491,3 +495,126 @@ def range_normal_loss(D, N, Dt, rows, cols, elev_min, elev_max, lambda_n=1.0):
             gP[r, c] -= gdx + gdy
     gD = np.einsum("hwk,hwk->hw", gP, V)
     return value, gD, gN
+
+
+# ---- map growth: densification masks and range-gradient-weighted sampling (Sec. 3.3.1-3.3.2) ----
+
+DENSIFY_QUANT = 256.0        # weights are counted in 1/256 m
+DENSIFY_EMPTY_LOGIT = -30.0  # opacity logit of a slot no pixel took (below alpha_min)
+
+
+def densify_weights(Dt, D, O, rows, cols, refine, lambda_do, lambda_de, w0, w_cap):
+    """Integer sampling weights q(u) of one view (rows x cols), binary32 arithmetic.
+    Mask: M_v = Dt > 0 (Sec. 3.3.1); in refinement also M_n or M_e (Sec. 3.3.2), M_n = O <=
+    lambda_do, M_e = |D - Dt| >= lambda_de.  Weight from the range gradients of the target:
+    g_x = Dt(r, c + 1 mod W) - Dt(r, c), g_y = Dt(r + 1, c) - Dt(r, c) (0 where a neighbour is
+    missing or invalid), w = min((w0 + |g_x|) + |g_y|, w_cap), q = floor(256 w) on the mask, else 0."""
+    f = np.float32
+    Dt = np.asarray(Dt, f).reshape(rows, cols)
+    valid = Dt > 0
+    m = valid.copy()
+    if refine:
+        D = np.asarray(D, f).reshape(rows, cols)
+        O = np.asarray(O, f).reshape(rows, cols)
+        m &= (O <= f(lambda_do)) | (np.abs(D - Dt) >= f(lambda_de))
+    right = np.roll(Dt, -1, 1)
+    gx = np.where(valid & np.roll(valid, -1, 1), right - Dt, f(0))
+    gy = np.zeros_like(Dt)
+    gy[:-1] = np.where(valid[:-1] & valid[1:], Dt[1:] - Dt[:-1], f(0))
+    w = np.minimum((f(w0) + np.abs(gx)) + np.abs(gy), f(w_cap))
+    q = np.floor(w * f(DENSIFY_QUANT)).astype(np.uint64)
+    return np.where(m, q, 0).astype(np.uint64).ravel()
+
+
+def densify_offset(Q, seed, call):
+    """The systematic-sampling offset o in [0, Q): x = first word of Philox((0, call, 2, 0),
+    (seed lo, seed hi)), o = floor(x Q / 2^32)."""
+    x = philox4x32_10((0, call, 2, 0), (seed & _U32, (seed >> 32) & _U32))[0]
+    return (x * int(Q)) >> 32
+
+
+def systematic_counts(q, n_d, o):
+    """Systematic (low-variance) weighted sampling of n_d points: with Q = sum q and the
+    exclusive prefix C, sample j sits at s_j = floor((j Q + o) / n_d) and pixel i takes the
+    samples with C_i <= s_j < C_i + q_i.  Returns (count per pixel, first sample index per pixel)
+    from the closed form #{j : s_j < X} = clamp(ceil((X n_d - o) / Q), 0, n_d).  Python integers."""
+    q = [int(x) for x in q]
+    Q = sum(q)
+    cnt = []
+    first = []
+    C = 0
+
+    def below(X):
+        t = X * n_d - o
+        return 0 if t <= 0 else min(n_d, -(-t // Q))
+
+    for qi in q:
+        a, b = below(C), below(C + qi)
+        first.append(a)
+        cnt.append(b - a)
+        C += qi
+    return np.array(cnt, np.int64), np.array(first, np.int64)
+
+
+def init_primitive(d, v_s, T_ws, dgamma, dtheta, scale_k, opacity):
+    """A new primitive from a sampled pixel (Sec. 3.3.1): centre T_ws (d v), normal towards the
+    sensor, t_n = -R_ws v, as the rotation of shortest arc from e_z (quaternion (w, x, y, z) =
+    (1 + n_z, -n_y, n_x, 0) normalised; (0, 1, 0, 0) when 1 + n_z < 1e-6), isotropic scale
+    scale_k d sqrt(dgamma dtheta), the given opacity.  Returns (pos_logit[4], quat[4],
+    log_scale[2]), FP64."""
+    T = np.asarray(T_ws, np.float64)
+    v = np.asarray(v_s, np.float64)
+    mu = T[:3, :3] @ (d * v) + T[:3, 3]
+    n = -(T[:3, :3] @ v)
+    n = n / np.linalg.norm(n)
+    if 1.0 + n[2] < 1e-6:
+        q = np.array([0.0, 1.0, 0.0, 0.0])
+    else:
+        q = np.array([1.0 + n[2], -n[1], n[0], 0.0])
+        q /= np.linalg.norm(q)
+    s = scale_k * d * math.sqrt(dgamma * dtheta)
+    return (np.array([*mu, math.log(opacity / (1.0 - opacity))]), q,
+            np.array([math.log(s), math.log(s)]))
+
+
+def densify(views, Dt, D, O, n_d, refine=False, lambda_do=0.5, lambda_de=0.1, w0=0.05,
+            w_cap=2.0, scale_k=2.0, opacity=0.5, seed=0, call=0):
+    """Map growth over the packed pixels of several views (each (T_ws, rows, cols, elev_min,
+    elev_max)): weights per view (densify_weights), one systematic draw of n_d samples over all
+    packed pixels, and a new primitive per slot.  A pixel drawn k >= 1 times fills the first of
+    its k slots; the other slots (all of them when no pixel is masked) are empty primitives
+    (centre 0, opacity logit -30, identity rotation, log-scales 0).  Returns (pos_logit (n_d, 4),
+    quat (n_d, 4), log_scale (n_d, 2), pixel of each slot (-1 for an empty slot))."""
+    qs, geo = [], []
+    off = 0
+    for (T, rows, cols, emin, emax) in views:
+        P = rows * cols
+        sl = slice(off, off + P)
+        qs.append(densify_weights(Dt[sl], None if D is None else D[sl],
+                                  None if O is None else O[sl], rows, cols, refine, lambda_do,
+                                  lambda_de, w0, w_cap))
+        geo.append((T, rows, cols, emin, emax, off))
+        off += P
+    q = np.concatenate(qs)
+    pl = np.zeros((n_d, 4))
+    pl[:, 3] = DENSIFY_EMPTY_LOGIT
+    qt = np.zeros((n_d, 4))
+    qt[:, 0] = 1.0
+    ls = np.zeros((n_d, 2))
+    pix = np.full(n_d, -1, np.int64)
+    Q = int(q.sum())
+    if Q == 0 or n_d == 0:
+        return pl, qt, ls, pix
+    o = densify_offset(Q, seed, call)
+    cnt, first = systematic_counts(q, n_d, o)
+    Dt64 = np.asarray(Dt, np.float32).astype(np.float64)
+    for (T, rows, cols, emin, emax, base) in geo:
+        V = pixel_rays(rows, cols, emin, emax).reshape(-1, 3)
+        dg = 2.0 * math.pi / cols
+        dt = (emax - emin) / (rows - 1) if rows > 1 else dg
+        for k in np.nonzero(cnt[base:base + rows * cols])[0]:
+            j = int(first[base + k])
+            pl[j], qt[j], ls[j] = init_primitive(Dt64[base + k], V[k], T, dg, dt, scale_k,
+                                                 opacity)
+            pix[j] = base + k
+    return pl, qt, ls, pix
