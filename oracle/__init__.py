@@ -458,7 +458,9 @@ def range_normal_loss(D, N, Dt, rows, cols, elev_min, elev_max, lambda_n=1.0):
     for pixel u = (r, c) with r + 1 < H, x = (r, c + 1 mod W) and y = (r + 1, c) (the azimuth
     wraps), P(w) = D(w) v(w) with v the pixel-centre ray, m = (P(x) - P(u)) x (P(y) - P(u)),
     n_D = -sign(m . v(u)) m / |m| (facing the sensor); the term lambda_n (1 - N(u) . n_D) counts
-    where the targets of u, x and y are valid (Dt > 0) and m != 0.  D and N are used as rendered
+    where the targets of u, x and y are valid (Dt > 0), their rendered ranges are positive (a
+    zero range puts P at the sensor, where m . v(u) vanishes and the side is undefined) and
+    m != 0.  D and N are used as rendered
     (unnormalised blends).  Returns (value, dL/dD (H, W), dL/dN (3, H, W)), FP64; the sign
     is held fixed in the gradient."""
     D = np.asarray(D, np.float64).reshape(rows, cols)
@@ -474,6 +476,8 @@ def range_normal_loss(D, N, Dt, rows, cols, elev_min, elev_max, lambda_n=1.0):
         for c in range(cols):
             cx = (c + 1) % cols
             if not (Dt[r, c] > 0 and Dt[r, cx] > 0 and Dt[r + 1, c] > 0):
+                continue
+            if not (D[r, c] > 0 and D[r, cx] > 0 and D[r + 1, c] > 0):
                 continue
             dx = P[r, cx] - P[r, c]
             dy = P[r + 1, c] - P[r, c]

@@ -60,3 +60,22 @@ def test_finite_differences_in_depth_and_normal():
               oracle.range_normal_loss(D, b, Dt, rows, cols, emin, emax, 1.3)[0]) / (2 * h)
         assert abs(fd - gN[k, r, c]) <= 1e-7 * max(1.0, abs(gN[k, r, c]))
     assert gD[2, 5] != 0.0 or gD[1, 5] != 0.0   # invalid target only removes its own stencils
+
+
+def test_zero_rendered_range_removes_its_stencils():
+    """A pixel with D = 0 sits at the sensor: the stencils that use it (as u, x or y) do not
+    count, and no gradient reaches it from them."""
+    rows, cols, emin, emax = 4, 10, -0.2, 0.2
+    rng = np.random.default_rng(9)
+    D = 5.0 + rng.normal(0, 0.2, (rows, cols))
+    N = rng.normal(0, 1, (3, rows, cols))
+    Dt = np.ones((rows, cols))
+    D[1, 4] = 0.0
+    val, gD, gN = oracle.range_normal_loss(D, N, Dt, rows, cols, emin, emax)
+    for (r, c) in [(1, 4), (1, 3), (0, 4)]:   # u, the stencil whose x it is, whose y it is
+        assert (gN[:, r, c] == 0).all()
+    assert gD[1, 4] == 0.0
+    full = (rows - 1) * cols
+    assert np.isfinite(val)
+    cnt = int((np.abs(gN).sum(0) > 0).sum())
+    assert cnt == full - 3
