@@ -23,6 +23,9 @@ Parity status per function (what pins it is in ``tests/test_oracle_*.py``):
                              of the sample points, evenly spaced picks on flat weights, masks by
                              their definitions, a step edge's weight, selection frequencies over
                              many draws; new primitives by round trip through the projection)
+  photometric_normal_eqs   : pinned (zero residual at the true pose, Jacobian by finite
+                             differences of the pose, Huber weights by hand, Gauss-Newton
+                             recovering a known pose offset on a synthetic scene)
 """
 from __future__ import annotations
 
@@ -622,3 +625,80 @@ def densify(views, Dt, D, O, n_d, refine=False, lambda_do=0.5, lambda_de=0.1, w0
                                                  opacity)
             pix[j] = base + k
     return pl, qt, ls, pix
+
+
+# ---- photometric registration residual (Sec. 3.4, Eq. L_photo) ---------------------------------
+
+def _se3_right_jacobian_point(R, p):
+    """d(R exp(xi^) p + t)/d xi at xi = 0 for xi = (rho, omega): R [I, -[p]x]  (3 x 6)."""
+    px = np.array([[0.0, -p[2], p[1]], [p[2], 0.0, -p[0]], [-p[1], p[0], 0.0]])
+    return R @ np.hstack([np.eye(3), -px])
+
+
+def photometric_normal_eqs(D, O, Dq, T_qm, rows, cols, elev_min, elev_max, o_min, huber_delta):
+    """Photometric residual of the rendered range image against a query range image of the same
+    sensor model, and its Gauss-Newton normal equations in the pose (Sec. 3.4, Eq. L_photo).
+    Reading: pixel u of the render with O(u) >= o_min has range d = D / O and point p = d v(u);
+    p' = T_qm p (render frame -> query frame); u' = phi(p') has the continuous column
+    c' = (pi - atan2(y', x')) / dgamma - 1/2 and row r' = (elev_max - atan2(z', |x'y'|)) /
+    dtheta; Dq is sampled bilinearly at u' (columns wrap; the four pixels must exist and have
+    Dq > 0); the residual is r = |p'| - Dq(u') (at T_qm = I it is d(u) - Dq(u)).  The pose is
+    perturbed on the right, T_qm exp(xi^), xi = (rho, omega); J = dr/dxi.  Huber weights
+    w = min(1, delta / |r|) (IRLS), cost rho_H(r).  Returns a dict: H = sum w J J^T (6 x 6),
+    g = sum w J r, cost, count, and per pixel r, w, J (P x 6), used (bool).  FP64."""
+    D = np.asarray(D, np.float64).ravel()
+    O = np.asarray(O, np.float64).ravel()
+    Dq = np.asarray(Dq, np.float64).reshape(rows, cols)
+    T = np.asarray(T_qm, np.float64)
+    R, t = T[:3, :3], T[:3, 3]
+    V = pixel_rays(rows, cols, elev_min, elev_max).reshape(-1, 3)
+    dg = 2.0 * math.pi / cols
+    dth = (elev_max - elev_min) / (rows - 1) if rows > 1 else dg
+    P = rows * cols
+    res = np.zeros(P)
+    wts = np.zeros(P)
+    J = np.zeros((P, 6))
+    used = np.zeros(P, bool)
+    H = np.zeros((6, 6))
+    g = np.zeros(6)
+    cost = 0.0
+    for i in range(P):
+        if not (O[i] >= o_min):
+            continue
+        d = D[i] / O[i]
+        p = d * V[i]
+        q = R @ p + t
+        x, y, z = q
+        rxy2 = x * x + y * y
+        rho = math.sqrt(rxy2 + z * z)
+        if rxy2 == 0.0:
+            continue
+        rxy = math.sqrt(rxy2)
+        cp = (math.pi - math.atan2(y, x)) / dg - 0.5
+        rp = (elev_max - math.atan2(z, rxy)) / dth if rows > 1 else 0.0
+        r0 = math.floor(rp)
+        if r0 < 0 or r0 + 1 >= rows:
+            continue
+        c0 = math.floor(cp)
+        fr, fc = rp - r0, cp - c0
+        ca, cb = c0 % cols, (c0 + 1) % cols
+        q00, q01, q10, q11 = Dq[r0, ca], Dq[r0, cb], Dq[r0 + 1, ca], Dq[r0 + 1, cb]
+        if not (q00 > 0 and q01 > 0 and q10 > 0 and q11 > 0):
+            continue
+        sample = (1 - fr) * ((1 - fc) * q00 + fc * q01) + fr * ((1 - fc) * q10 + fc * q11)
+        dS_dc = (1 - fr) * (q01 - q00) + fr * (q11 - q10)
+        dS_dr = (1 - fc) * (q10 - q00) + fc * (q11 - q01)
+        dc_dq = np.array([y, -x, 0.0]) / (dg * rxy2)
+        dth_dq = np.array([-z * x / (rxy * rho * rho), -z * y / (rxy * rho * rho), rxy / (rho * rho)])
+        dr_dq = -dth_dq / dth
+        dres_dq = q / rho - (dS_dc * dc_dq + dS_dr * dr_dq)
+        Ji = dres_dq @ _se3_right_jacobian_point(R, p)
+        r = rho - sample
+        a = abs(r)
+        w = 1.0 if a <= huber_delta else huber_delta / a
+        cost += 0.5 * r * r if a <= huber_delta else huber_delta * (a - 0.5 * huber_delta)
+        H += w * np.outer(Ji, Ji)
+        g += w * Ji * r
+        res[i], wts[i], J[i], used[i] = r, w, Ji, True
+    return {"H": H, "g": g, "cost": cost, "count": int(used.sum()), "r": res, "w": wts, "J": J,
+            "used": used}
