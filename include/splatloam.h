@@ -111,11 +111,41 @@ typedef struct {
 
 /* Loss weights of Eq. loss_full (rho_d = 1): o_eps floors O inside -log O.  lambda_s and tau_s
  * weigh the scale term of splat_refine_step, lambda_s sum_i max(0, max(s_a, s_b)_i - tau_s) (the
- * penalty of Eq. L_s with its sign read as growth beyond tau_s; 0 disables it). */
+ * penalty of Eq. L_s with its sign read as growth beyond tau_s; 0 disables it).
+ * normal_mode selects the normal term of Eq. loss_normal:
+ *   SPLAT_NORMALS_TARGET (0): lambda_n (1 - N(u) . Nt(u)) against the target normals;
+ *   SPLAT_NORMALS_RANGE_MAP (1): self-regularised, lambda_n (1 - N(u) . n_D(u)) with n_D the
+ *     normal of the rendered range map D (after 2DGS): for u = (r, c), r + 1 < rows,
+ *     x = (r, c + 1 mod cols), y = (r + 1, c), P(w) = D(w) v(w) (v the pixel-centre ray),
+ *     m = (P(x) - P(u)) x (P(y) - P(u)), n_D = -sign(m . v(u)) m / |m| (facing the sensor),
+ *     counted where the targets of u, x and y are valid, D > 0 at all three and m != 0 (a zero
+ *     range puts P at the sensor, where the side is undefined; the sign is held fixed in the
+ *     gradient, which reaches D at u, x and y).  Needs the views' geometry: splat_view_loss and
+ *     splat_refine_step only; target_normal may be NULL there. */
+enum { SPLAT_NORMALS_TARGET = 0, SPLAT_NORMALS_RANGE_MAP = 1 };
 typedef struct {
     float lambda_n, lambda_o, o_eps;
     float lambda_s, tau_s;
+    int32_t normal_mode;
 } splat_loss_config;
+
+/* Map growth (Sec. 3.3.1 local model initialisation, Sec. 3.3.2 densification).
+ *   refine = 0: the mask is M_v (target range > 0); refine = 1: M_v and (M_n or M_e), with
+ *     M_n = O <= lambda_do and M_e = |D - Dt| >= lambda_de on the rendered images (binary32).
+ *   Weight of a masked pixel from the range gradients of the target: g_x = Dt(r, c + 1 mod W) -
+ *     Dt(r, c), g_y = Dt(r + 1, c) - Dt(r, c) (0 where a neighbour is missing or invalid),
+ *     w = min((w0 + |g_x|) + |g_y|, w_cap) in binary32, counted as q = floor(256 w).
+ *   New primitive of a drawn pixel: centre T_ws (Dt v), normal towards the sensor (the
+ *     shortest-arc rotation from e_z to -R_ws v; (0, 1, 0, 0) when that normal is -e_z within
+ *     1e-6), log-scales log(scale_k Dt sqrt(dgamma dtheta)) on both axes, opacity `opacity`.
+ *   seed: key of the Philox-4x32-10 stream of the draw. */
+typedef struct {
+    int32_t refine;
+    float lambda_do, lambda_de;
+    float w0, w_cap;          /* metres; 0 <= w0, 0 < w_cap <= 16 */
+    float scale_k, opacity;   /* scale_k > 0, 0 < opacity < 1      */
+    uint64_t seed;
+} splat_densify_config;
 
 /* Adam settings; one learning rate per parameter group. */
 typedef struct {
@@ -242,13 +272,57 @@ SPLAT_API int splat_get_active_views(splat_ctx *ctx, uint8_t *flags);
 SPLAT_API int splat_backproject(splat_ctx *ctx, const float *depth, const float *alpha,
                                 float o_min, float *points, void *stream);
 
+/* Map growth over the packed pixels of the registered views (Sec. 3.3.1, 3.3.2): the mask and
+ * weights of splat_densify_config, then one systematic weighted draw of n_new samples over all
+ * packed pixels (Q = sum of the weights q, C_i the exclusive prefix in packed order; sample j
+ * sits at s_j = floor((j Q + o) / n_new) and belongs to the pixel with C_i <= s_j < C_i + q_i;
+ * o = floor(x Q / 2^32) with x the first word of Philox-4x32-10((0, c, 2, 0), (seed lo, seed
+ * hi)), c the number of earlier splat_densify calls on this context).  Slot j of the new
+ * primitives, index n_old + j of pos_logit [capacity][4], quat [capacity][4] and log_scale
+ * [capacity][2] (device, caller-owned), receives the primitive of the pixel whose first sample
+ * is j; a slot whose sample falls on a pixel drawn before it, and every slot when no pixel is
+ * masked, is written empty (centre 0, opacity logit -30: below alpha_min, so it takes no pairs
+ * and no gradient; identity rotation; log-scales 0).  The caller zeroes the optimiser moments of
+ * the new slots.  target_depth [P]; depth and alpha [P] (as rendered) are read when
+ * cfg->refine.  Stream-ordered, no synchronisation or allocation (capturable); uses the
+ * context's gradient-image workspace as scratch.  Errors: INVALID_ARG (null pointer, n_new >
+ * 2^24, n_old + n_new > capacity, settings out of range, n_pixels * 4096 * n_new >= 9e18), STATE
+ * (no views), CUDA. */
+SPLAT_API int splat_densify(splat_ctx *ctx, const float *target_depth, const float *depth,
+                            const float *alpha, const splat_densify_config *cfg, int64_t n_new,
+                            float *pos_logit, float *quat, float *log_scale, int64_t n_old,
+                            int64_t capacity, void *stream);
+
+/* Photometric registration residual of a rendered view against a query range image of the same
+ * sensor model, with its Gauss-Newton normal equations in the pose (Sec. 3.4, Eq. L_photo; the
+ * pose update T <- T exp(delta) of that section).  For pixel u of view `view` with
+ * O(u) >= o_min: d = D / O, p = d v(u) (render frame), p' = T p (query frame),
+ * u' = phi(p') with continuous column c' = (pi - atan2(y', x')) / dgamma - 1/2 and row
+ * r' = (elev_max - atan2(z', |x'y'|)) / dtheta; query_depth is sampled bilinearly at u'
+ * (columns wrap; the four pixels must exist and be > 0); r = |p'| - Dq(u') (at T = I the
+ * printed D(u) - Dq(u) with D read as the range d); J = dr/dxi for T exp(xi^), xi = (rho,
+ * omega) in the render frame; Huber IRLS weight w = min(1, huber_delta / |r|).
+ * depth, alpha, query_depth: device, the view's rows x cols pixels (for the packed images, the
+ * pointer plus the view's first pixel).  T_qm: device float[12], row-major 3 x 4 [R | t]
+ * (device-resident so a capturable Gauss-Newton loop can update it).  normal_eqs: device
+ * double[29], written: H = sum w J J^T upper triangle row-major (21), g = sum w J r (6), the
+ * Huber cost sum, the number of pixels used.  per_pixel (nullable): device float[8][P] planar,
+ * r, w, J (zeros where a pixel is not used).  Stream-ordered, no allocation.
+ * Errors: INVALID_ARG (null pointer, view out of range, o_min or huber_delta <= 0), STATE (no
+ * views), CUDA. */
+SPLAT_API int splat_photometric(splat_ctx *ctx, int32_t view, const float *depth,
+                                const float *alpha, const float *query_depth, const float *T_qm,
+                                float o_min, float huber_delta, double *normal_eqs,
+                                float *per_pixel, void *stream);
+
 /* ---- loss and optimiser ------------------------------------------------------------------- */
 
 /* Per-pixel loss over n_pixels packed pixels (depth/alpha/target_depth [P], normal and
  * target_normal [3][P] planar with plane stride n_pixels): valid pixels are those with
  * target_depth > 0 (M_v); L = sum |D - Dt| + lambda_n (1 - N . Nt) + lambda_o (-log max(O,
  * o_eps)).  Writes dL_ddepth, dL_dnormal (3 x P), dL_dalpha (0 outside M_v), and ADDS L to
- * *loss_out (device double; caller zeroes it).  Errors: INVALID_ARG, CUDA. */
+ * *loss_out (device double; caller zeroes it).  cfg->normal_mode must be SPLAT_NORMALS_TARGET
+ * (the range-map mode needs the views: splat_view_loss).  Errors: INVALID_ARG, CUDA. */
 SPLAT_API int splat_loss(const float *depth, const float *normal, const float *alpha,
                          const float *target_depth, const float *target_normal,
                          int64_t n_pixels, const splat_loss_config *cfg, float *dL_ddepth,
@@ -258,6 +332,17 @@ SPLAT_API int splat_loss(const float *depth, const float *normal, const float *a
  * their gradients (same layout), first and second moments m_*, v_* (same layouts, caller-owned,
  * zero before the first step) and a device int32 step counter that the call increments
  * (the update uses t = *step + 1).  Errors: INVALID_ARG, CUDA. */
+/* The loss of splat_loss over the packed images of the context's registered views (P =
+ * ctx's pixel count), with either normal mode of splat_loss_config; every registered view counts
+ * (keyframe sampling applies inside splat_refine_step only).  target_normal may be NULL when
+ * cfg->normal_mode = SPLAT_NORMALS_RANGE_MAP.  ADDS L to *loss_out.  Stream-ordered.
+ * Errors: INVALID_ARG (null pointer, unknown mode), STATE (no views), CUDA. */
+SPLAT_API int splat_view_loss(splat_ctx *ctx, const float *depth, const float *normal,
+                              const float *alpha, const float *target_depth,
+                              const float *target_normal, const splat_loss_config *cfg,
+                              float *dL_ddepth, float *dL_dnormal, float *dL_dalpha,
+                              double *loss_out, void *stream);
+
 SPLAT_API int splat_adam_step(float *pos_logit, float *quat, float *log_scale,
                               const float *g_pos_logit, const float *g_quat,
                               const float *g_log_scale, float *m_pos_logit, float *m_quat,

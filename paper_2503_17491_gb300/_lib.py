@@ -41,7 +41,14 @@ class splat_capacity(ctypes.Structure):
 class splat_loss_config(ctypes.Structure):
     _fields_ = [("lambda_n", ctypes.c_float), ("lambda_o", ctypes.c_float),
                 ("o_eps", ctypes.c_float), ("lambda_s", ctypes.c_float),
-                ("tau_s", ctypes.c_float)]
+                ("tau_s", ctypes.c_float), ("normal_mode", ctypes.c_int32)]
+
+
+class splat_densify_config(ctypes.Structure):
+    _fields_ = [("refine", ctypes.c_int32), ("lambda_do", ctypes.c_float),
+                ("lambda_de", ctypes.c_float), ("w0", ctypes.c_float), ("w_cap", ctypes.c_float),
+                ("scale_k", ctypes.c_float), ("opacity", ctypes.c_float),
+                ("seed", ctypes.c_uint64)]
 
 
 class splat_adam_config(ctypes.Structure):
@@ -80,6 +87,11 @@ SIGNATURES = {
                                _P], _I),
     "splat_loss": ([_P, _P, _P, _P, _P, _I64, ctypes.POINTER(splat_loss_config), _P, _P, _P, _P,
                     _P], _I),
+    "splat_photometric": ([_P, _I32, _P, _P, _P, _P, ctypes.c_float, ctypes.c_float, _P, _P,
+                           _P], _I),
+    "splat_densify": ([_P] * 4 + [ctypes.POINTER(splat_densify_config), _I64] + [_P] * 3
+                      + [_I64, _I64, _P], _I),
+    "splat_view_loss": ([_P] * 6 + [ctypes.POINTER(splat_loss_config)] + [_P] * 5, _I),
     "splat_adam_step": ([_P] * 13 + [_I64, ctypes.POINTER(splat_adam_config), _P], _I),
     "splat_refine_step": ([_P, _P, _P, _P, _I64, _P, _P, ctypes.POINTER(splat_loss_config),
                            ctypes.POINTER(splat_adam_config)] + [_P] * 9, _I),

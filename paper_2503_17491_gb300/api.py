@@ -78,10 +78,30 @@ class LossConfig:
     o_eps: float = 1e-6
     lambda_s: float = 0.0   # scale term (splat_refine_step only)
     tau_s: float = 0.5
+    normal_mode: int = 0    # 0: against target normals; 1: normals of the rendered range map
 
     def c(self):
         return _lib.splat_loss_config(self.lambda_n, self.lambda_o, self.o_eps, self.lambda_s,
-                                      self.tau_s)
+                                      self.tau_s, self.normal_mode)
+
+
+@dataclass
+class DensifyConfig:
+    """Map growth settings (splat_densify_config): refine = False uses the valid mask only
+    (local model initialisation); True adds M_n (O <= lambda_do) or M_e (|D - Dt| >= lambda_de)."""
+    refine: bool = False
+    lambda_do: float = 0.5
+    lambda_de: float = 0.1
+    w0: float = 0.05
+    w_cap: float = 2.0
+    scale_k: float = 2.0
+    opacity: float = 0.5
+    seed: int = 0
+
+    def c(self):
+        return _lib.splat_densify_config(int(self.refine), self.lambda_do, self.lambda_de,
+                                         self.w0, self.w_cap, self.scale_k, self.opacity,
+                                         self.seed)
 
 
 @dataclass
@@ -204,6 +224,54 @@ class SplatContext:
             _ptr(m_pl), _ptr(m_q), _ptr(m_ls), _ptr(v_pl), _ptr(v_q), _ptr(v_ls), _ptr(step),
             _ptr(loss_out), _stream(stream)), "splat_refine_step")
 
+    def view_loss(self, depth, normal, alpha, target_depth, target_normal=None,
+                  cfg: LossConfig | None = None, stream=None):
+        """The loss over the packed images of the registered views (splat_view_loss), either
+        normal mode; returns (L (device double tensor), dL/dD, dL/dN, dL/dO)."""
+        cfg = cfg or LossConfig()
+        gD = torch.empty_like(depth)
+        gN = torch.empty_like(normal)
+        gO = torch.empty_like(alpha)
+        L = torch.zeros(1, dtype=torch.float64, device=depth.device)
+        _lib.check(self.lib.splat_view_loss(
+            self.h, _ptr(depth), _ptr(normal), _ptr(alpha), _ptr(target_depth),
+            _ptr(target_normal), ctypes.byref(cfg.c()),
+            _ptr(gD), _ptr(gN), _ptr(gO), _ptr(L), _stream(stream)), "splat_view_loss")
+        return L, gD, gN, gO
+
+    def densify(self, params, n_old: int, n_new: int, target_depth, depth=None, alpha=None,
+                cfg: DensifyConfig | None = None, stream=None):
+        """Write n_new primitives drawn from the packed target range image into rows
+        [n_old, n_old + n_new) of params (pos_logit, quat, log_scale, each with room for them):
+        splat_densify.  Empty slots carry opacity logit -30."""
+        cfg = cfg or DensifyConfig()
+        pl, q, ls = params
+        for t, w in ((pl, 4), (q, 4), (ls, 2)):
+            _f32(t, (w,))
+        cap = min(pl.shape[0], q.shape[0], ls.shape[0])
+        _lib.check(self.lib.splat_densify(
+            self.h, _ptr(target_depth), _ptr(depth), _ptr(alpha), ctypes.byref(cfg.c()),
+            int(n_new), _ptr(pl), _ptr(q), _ptr(ls), int(n_old), int(cap), _stream(stream)),
+            "splat_densify")
+
+    def photometric(self, view: int, depth, alpha, query_depth, T_qm, o_min=0.5, huber_delta=0.2,
+                    per_pixel=False, out=None, stream=None):
+        """Photometric residual of registered view `view` (its own rows x cols pixels) against a
+        query range image, reduced to Gauss-Newton normal equations (splat_photometric).
+        T_qm: device float32 (3, 4) [R | t], render frame -> query frame.  Returns the device
+        double[29] (see unpack_normal_eqs) and, when per_pixel, the (8, P) float32 r, w, J."""
+        out = out if out is not None else torch.empty(29, dtype=torch.float64,
+                                                      device=depth.device)
+        P = self.views[view].rows * self.views[view].cols
+        px = torch.empty(8, P, dtype=torch.float32, device=depth.device) if per_pixel else None
+        if T_qm.dtype != torch.float32 or tuple(T_qm.shape) != (3, 4) or not T_qm.is_cuda:
+            raise ValueError("T_qm: float32 CUDA tensor of shape (3, 4)")
+        _lib.check(self.lib.splat_photometric(
+            self.h, int(view), _ptr(depth), _ptr(alpha), _ptr(query_depth),
+            _ptr(T_qm.contiguous()), float(o_min), float(huber_delta), _ptr(out), _ptr(px),
+            _stream(stream)), "splat_photometric")
+        return (out, px) if per_pixel else out
+
     # ---- inspection ---------------------------------------------------------------------
     def set_view_sampling(self, draws: int, p_newest: float = 0.4, seed: int = 0):
         """Draw `draws` keyframes per render from the truncated geometric law over keyframe age
@@ -303,6 +371,18 @@ def loss(depth, normal, alpha, target_depth, target_normal, cfg: LossConfig | No
                               _ptr(target_normal), P, ctypes.byref(cfg.c()), _ptr(gD), _ptr(gN),
                               _ptr(gO), _ptr(L), _stream(stream)), "splat_loss")
     return L, gD, gN, gO
+
+
+def unpack_normal_eqs(v):
+    """(H (6, 6), g (6,), cost, count) from the 29 values of splat_photometric."""
+    v = np.asarray(v.cpu() if hasattr(v, "cpu") else v, np.float64)
+    H = np.zeros((6, 6))
+    k = 0
+    for a in range(6):
+        for b in range(a, 6):
+            H[a, b] = H[b, a] = v[k]
+            k += 1
+    return H, v[21:27].copy(), float(v[27]), int(round(v[28]))
 
 
 def adam_state(n, device="cuda"):

@@ -27,6 +27,8 @@ UNITS = {
     "splat_sort.cu": [],
     "splat_render.cu": [],
     "splat_optim.cu": [],
+    "splat_grow.cu": ["-fmad=false"],
+    "splat_photo.cu": [],
     "splat_abi.cu": [],
     "splat_noalloc.cu": [],
 }

@@ -100,7 +100,9 @@ struct splat_ctx {
     float *d_gimg = nullptr;    // refine: their gradients
     uint32_t *d_counters = nullptr;   // [0] pairs M, [1] status, [2] queue f, [3] queue b,
                                       // [4] (view, primitive) pairs that touch a tile,
-                                      // [5] record chunks taken, [7] sampling step
+                                      // [5] record chunks taken, [6] map-growth draws,
+                                      // [7] sampling step
+    unsigned long long *d_grow_sums = nullptr;  // map growth: block sums, Q, offset
     unsigned long long *d_evals = nullptr;      // [0] forward, [1] backward
 
     // profiling events around the compositing kernels: [0,1] forward, [2,3] backward
@@ -282,7 +284,7 @@ void free_ctx(splat_ctx *c)
                     c->d_dkeys2, c->d_dvals2, c->d_tkeys, c->d_tvals, c->d_tkeys2, c->d_tvals2,
                     c->d_block_sums, c->d_hist, c->d_ranges, c->d_tfinal, c->d_nlast, c->d_wgrad,
                     c->d_pose, c->d_rec, c->d_rec_prev, c->d_rec_head, c->d_rec_fill,
-                    c->d_samp_thr, c->d_active,
+                    c->d_samp_thr, c->d_active, c->d_grow_sums,
                     c->d_img, c->d_gimg, c->d_counters, c->d_evals, c->d_pixframes,
                     c->d_tileinfo, c->d_tile_order};
     for (void *p : ptrs)
@@ -380,6 +382,7 @@ SPLAT_API int splat_ctx_create(const splat_render_config *cfg, const splat_capac
     if (e == cudaSuccess) e = dalloc(&c->d_pose, static_cast<size_t>(cap->max_views) * 6);
     if (e == cudaSuccess) e = dalloc(&c->d_samp_thr, static_cast<size_t>(splat::kMaxViews));
     if (e == cudaSuccess) e = dalloc(&c->d_active, static_cast<size_t>(cap->max_views));
+    if (e == cudaSuccess) e = dalloc(&c->d_grow_sums, static_cast<size_t>(splat::kGrowMaxGrid + 2));
     // contributor records: at most one per (block, staged entry); the pool takes two per
     // (tile, primitive) pair of capacity plus one partial chunk per work item
     const int64_t items = TT * (splat::kBlock / 32);
@@ -658,17 +661,106 @@ SPLAT_API int splat_backproject(splat_ctx *ctx, const float *depth, const float 
     return SPLAT_OK;
 }
 
+SPLAT_API int splat_photometric(splat_ctx *ctx, int32_t view, const float *depth,
+                                const float *alpha, const float *query_depth, const float *T_qm,
+                                float o_min, float huber_delta, double *normal_eqs,
+                                float *per_pixel, void *stream)
+{
+    if (!ctx || !depth || !alpha || !query_depth || !T_qm || !normal_eqs || !(o_min > 0.0f) ||
+        !(huber_delta > 0.0f))
+        return SPLAT_ERR_INVALID_ARG;
+    if (view < 0 || view >= ctx->n_views) return ctx->n_views < 1 ? SPLAT_ERR_STATE
+                                                                   : SPLAT_ERR_INVALID_ARG;
+    CK(splat::launch_photometric(ctx->views[view], depth, alpha, query_depth, T_qm, o_min,
+                                 huber_delta, normal_eqs, per_pixel, ctx->sms,
+                                 static_cast<cudaStream_t>(stream)));
+    ctx->launches += 1;
+    return SPLAT_OK;
+}
+
+SPLAT_API int splat_densify(splat_ctx *ctx, const float *target_depth, const float *depth,
+                            const float *alpha, const splat_densify_config *cfg, int64_t n_new,
+                            float *pos_logit, float *quat, float *log_scale, int64_t n_old,
+                            int64_t capacity, void *stream)
+{
+    if (!ctx || !target_depth || !cfg || !pos_logit || !quat || !log_scale || n_new < 0 ||
+        n_old < 0 || n_new > (int64_t{1} << 24) || n_old + n_new > capacity)
+        return SPLAT_ERR_INVALID_ARG;
+    if (cfg->refine && (!depth || !alpha)) return SPLAT_ERR_INVALID_ARG;
+    if (!(cfg->w0 >= 0.0f) || !(cfg->w_cap > 0.0f && cfg->w_cap <= 16.0f) ||
+        !(cfg->scale_k > 0.0f) || !(cfg->opacity > 0.0f && cfg->opacity < 1.0f) ||
+        !std::isfinite(cfg->lambda_do) || !std::isfinite(cfg->lambda_de))
+        return SPLAT_ERR_INVALID_ARG;
+    if (ctx->n_views < 1) return SPLAT_ERR_STATE;
+    // the integer draw needs n_pixels * max weight * n_new < 2^63 (max weight 16 * 256)
+    if (ctx->n_pixels > 0 && n_new > 0 &&
+        static_cast<double>(ctx->n_pixels) * 4096.0 * static_cast<double>(n_new) >= 9.0e18)
+        return SPLAT_ERR_INVALID_ARG;
+    splat::GrowArgs a{};
+    a.views = ctx->d_views;
+    a.n_views = ctx->n_views;
+    a.n_pixels = ctx->n_pixels;
+    a.t_depth = target_depth;
+    a.depth = depth;
+    a.alpha = alpha;
+    a.refine = cfg->refine ? 1 : 0;
+    a.lambda_do = cfg->lambda_do;
+    a.lambda_de = cfg->lambda_de;
+    a.w0 = cfg->w0;
+    a.w_cap = cfg->w_cap;
+    a.scale_k = cfg->scale_k;
+    a.logit = static_cast<float>(std::log(static_cast<double>(cfg->opacity) /
+                                          (1.0 - static_cast<double>(cfg->opacity))));
+    a.empty_logit = -30.0f;
+    a.seed_lo = static_cast<uint32_t>(cfg->seed);
+    a.seed_hi = static_cast<uint32_t>(cfg->seed >> 32);
+    a.call = ctx->d_counters + 6;
+    a.q = reinterpret_cast<uint32_t *>(ctx->d_gimg);
+    a.block_sums = ctx->d_grow_sums;
+    a.pos_logit = reinterpret_cast<float4 *>(pos_logit) + n_old;
+    a.quat = reinterpret_cast<float4 *>(quat) + n_old;
+    a.log_scale = reinterpret_cast<float2 *>(log_scale) + n_old;
+    a.n_d = n_new;
+    CK(splat::launch_grow(a, static_cast<cudaStream_t>(stream)));
+    if (n_new > 0) ctx->launches += 3;
+    return SPLAT_OK;
+}
+
 SPLAT_API int splat_loss(const float *depth, const float *normal, const float *alpha,
                          const float *target_depth, const float *target_normal,
                          int64_t n_pixels, const splat_loss_config *cfg, float *dL_ddepth,
                          float *dL_dnormal, float *dL_dalpha, double *loss_out, void *stream)
 {
     if (!depth || !normal || !alpha || !target_depth || !target_normal || !cfg || !dL_ddepth ||
-        !dL_dnormal || !dL_dalpha || !loss_out || n_pixels < 0)
+        !dL_dnormal || !dL_dalpha || !loss_out || n_pixels < 0 ||
+        cfg->normal_mode != SPLAT_NORMALS_TARGET)
         return SPLAT_ERR_INVALID_ARG;
     CK(splat::launch_loss(depth, normal, alpha, target_depth, target_normal, n_pixels,
                           cfg->lambda_n, cfg->lambda_o, cfg->o_eps, dL_ddepth, dL_dnormal,
                           dL_dalpha, loss_out, static_cast<cudaStream_t>(stream)));
+    return SPLAT_OK;
+}
+
+static bool loss_cfg_ok(const splat_loss_config *cfg, const float *target_normal)
+{
+    if (cfg->normal_mode == SPLAT_NORMALS_TARGET) return target_normal != nullptr;
+    return cfg->normal_mode == SPLAT_NORMALS_RANGE_MAP;
+}
+
+SPLAT_API int splat_view_loss(splat_ctx *ctx, const float *depth, const float *normal,
+                              const float *alpha, const float *target_depth,
+                              const float *target_normal, const splat_loss_config *cfg,
+                              float *dL_ddepth, float *dL_dnormal, float *dL_dalpha,
+                              double *loss_out, void *stream)
+{
+    if (!ctx || !depth || !normal || !alpha || !target_depth || !cfg || !dL_ddepth ||
+        !dL_dnormal || !dL_dalpha || !loss_out || !loss_cfg_ok(cfg, target_normal))
+        return SPLAT_ERR_INVALID_ARG;
+    if (ctx->n_views < 1) return SPLAT_ERR_STATE;
+    CK(splat::launch_loss(depth, normal, alpha, target_depth, target_normal, ctx->n_pixels,
+                          cfg->lambda_n, cfg->lambda_o, cfg->o_eps, dL_ddepth, dL_dnormal,
+                          dL_dalpha, loss_out, static_cast<cudaStream_t>(stream), ctx->d_views,
+                          ctx->n_views, nullptr, cfg->normal_mode));
     return SPLAT_OK;
 }
 
@@ -718,8 +810,9 @@ SPLAT_API int splat_refine_step(splat_ctx *ctx, float *pos_logit, float *quat, f
                                 float *v_quat, float *v_log_scale, int32_t *step,
                                 double *loss_out, void *stream)
 {
-    if (!ctx || !target_depth || !target_normal || !loss_cfg || !adam_cfg || !m_pos_logit ||
-        !m_quat || !m_log_scale || !v_pos_logit || !v_quat || !v_log_scale || !step || !loss_out)
+    if (!ctx || !target_depth || !loss_cfg || !adam_cfg || !m_pos_logit || !m_quat ||
+        !m_log_scale || !v_pos_logit || !v_quat || !v_log_scale || !step || !loss_out ||
+        !loss_cfg_ok(loss_cfg, target_normal))
         return SPLAT_ERR_INVALID_ARG;
     if (ctx->n_views < 1) return SPLAT_ERR_STATE;
     splat_gaussians g{pos_logit, quat, log_scale, n};
@@ -735,7 +828,8 @@ SPLAT_API int splat_refine_step(splat_ctx *ctx, float *pos_logit, float *quat, f
     CK(splat::launch_loss(depth, normal, alpha, target_depth, target_normal, P, loss_cfg->lambda_n,
                           loss_cfg->lambda_o, loss_cfg->o_eps, gd, gn, ga, loss_out, st,
                           ctx->d_views, ctx->n_views,
-                          ctx->samp_draws > 0 ? ctx->d_active : nullptr));
+                          ctx->samp_draws > 0 ? ctx->d_active : nullptr,
+                          loss_cfg->normal_mode));
     r = backward_core(ctx, &g, gd, gn, ga, st);
     if (r) return r;
     splat::AdamArgs a{};

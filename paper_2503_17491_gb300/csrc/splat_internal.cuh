@@ -34,6 +34,36 @@ struct ViewDesc {
     float cull_t_top, cull_l_top, cull_t_bot, cull_l_bot;
 };
 
+// Pixel-centre ray of pixel (r, c) of a view (Sec. 3.1), binary32.
+__device__ __forceinline__ float3 pixel_ray(const ViewDesc &vd, int r, int c)
+{
+    const float g = 3.14159265358979f - vd.dgamma * (static_cast<float>(c) + 0.5f);
+    const float th = vd.rows > 1 ? vd.elev_max - vd.dtheta * static_cast<float>(r) : vd.elev_max;
+    float sg, cg, st, ct;
+    sincosf(g, &sg, &cg);
+    sincosf(th, &st, &ct);
+    return make_float3(ct * cg, ct * sg, st);
+}
+
+// Philox-4x32-10 (Salmon, Moraes, Dror, Shaw, SC 2011), from its definition: a round maps
+// (c0, c1, c2, c3) to (hi(M1 c2) ^ c1 ^ k0, lo(M1 c2), hi(M0 c0) ^ c3 ^ k1, lo(M0 c0)); the key
+// is bumped by the Weyl constants between rounds.
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k)
+{
+    constexpr uint32_t M0 = 0xD2511F53u, M1 = 0xCD9E8D57u, W0 = 0x9E3779B9u, W1 = 0xBB67AE85u;
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const uint32_t hi0 = __umulhi(M0, c.x), lo0 = M0 * c.x;
+        const uint32_t hi1 = __umulhi(M1, c.z), lo1 = M1 * c.z;
+        c = make_uint4(hi1 ^ c.y ^ k.x, lo1, hi0 ^ c.w ^ k.y, lo0);
+        if (r < 9) {
+            k.x += W0;
+            k.y += W1;
+        }
+    }
+    return c;
+}
+
 // Keyframe sampling (Sec. 3.3): draws j < draws of refinement step *step take the first word x of
 // Philox-4x32-10((j, step, 0, 0), (seed lo, seed hi)); the drawn view is n_views - 1 - #{a :
 // x >= thr[a]} (thr: n_views - 1 integer thresholds of the cumulative law); active[v] = 1 for a
@@ -47,6 +77,36 @@ cudaError_t launch_sample_views(int n_views, int draws, const uint32_t *thr, uin
 cudaError_t launch_backproject(const ViewDesc *views, int n_views, int64_t n_pixels,
                                const float *depth, const float *alpha, float o_min, float *points,
                                cudaStream_t st);
+
+// Map growth (Sec. 3.3.1, 3.3.2): mask, range-gradient weights and a systematic draw of n_d
+// pixels over the packed pixels of the views; slot j of the new primitives takes the pixel that
+// holds sample j first, or is written empty.
+constexpr int kGrowMaxGrid = 1024;
+struct GrowArgs {
+    const ViewDesc *views;
+    int n_views;
+    int64_t n_pixels;
+    const float *t_depth, *depth, *alpha;   // depth, alpha: used when refine != 0
+    int refine;
+    float lambda_do, lambda_de, w0, w_cap, scale_k, logit, empty_logit;
+    uint32_t seed_lo, seed_hi;
+    uint32_t *call;                         // device counter of draws, advanced per call
+    uint32_t *q;                            // scratch, n_pixels
+    unsigned long long *block_sums;         // scratch, kGrowMaxGrid + 2
+    float4 *pos_logit, *quat;               // the n_d new slots
+    float2 *log_scale;
+    int64_t n_d;
+    int grid;                               // set by launch_grow
+    int64_t chunk;
+};
+cudaError_t launch_grow(GrowArgs a, cudaStream_t st);
+
+// Photometric residual of one view against a query range image and its Gauss-Newton normal
+// equations (Sec. 3.4): out[29] = H upper triangle (21, row-major), g (6), Huber cost, count;
+// per_pixel (nullable) = 8 x P planar: r, w, J (6).  T: device binary32 3 x 4 render -> query.
+cudaError_t launch_photometric(const ViewDesc &vd, const float *depth, const float *alpha,
+                               const float *qdepth, const float *T, float o_min, float delta,
+                               double *out, float *per_pixel, int sms, cudaStream_t st);
 
 // the culling cones of a view (host)
 inline void set_cull_cones(ViewDesc &vd, double emin, double emax, double dtheta)
@@ -385,13 +445,14 @@ cudaError_t launch_param_grads(const float4 *pos_logit, const float4 *quat, cons
                                float2 *g_log_scale, int accumulate, cudaStream_t st);
 
 // active (nullable): pixels of views with active[v] == 0 count as invalid (views: the registered
-// views, for the pixel -> view lookup)
+// views, for the pixel -> view lookup).  normal_mode 0: normal term against t_normal; 1:
+// self-regularised against the normals of the rendered range map (needs views; t_normal unused)
 cudaError_t launch_loss(const float *depth, const float *normal, const float *alpha,
                         const float *t_depth, const float *t_normal, int64_t n_pixels,
                         float lambda_n, float lambda_o, float o_eps, float *g_depth,
                         float *g_normal, float *g_alpha, double *loss_out, cudaStream_t st,
                         const ViewDesc *views = nullptr, int n_views = 0,
-                        const uint8_t *active = nullptr);
+                        const uint8_t *active = nullptr, int normal_mode = 0);
 
 struct AdamArgs {
     float4 *pos_logit;

@@ -1,8 +1,9 @@
 // K8 (loss) and K9 (Adam, optionally fused with K7).
 //
 // Loss over the valid pixels M_v (target range > 0, Sec. 3.3.1): the L1 range term of
-// Eq. loss_range (rho_d = 1), the normal term of Eq. loss_normal taken against the target
-// normal, and optionally the opacity term of Eq. loss_opacity.  Per-pixel gradients are written
+// Eq. loss_range (rho_d = 1), the normal term of Eq. loss_normal taken either against the target
+// normal or against the normal of the rendered range map (self-regularised), and optionally the
+// opacity term of Eq. loss_opacity.  Per-pixel gradients are written
 // for the backward; the scalar is reduced per warp in binary32 and per CTA in binary64.
 //
 // Adam: the paper does not name its optimiser; a bias-corrected Adam with one learning rate per
@@ -16,6 +17,73 @@
 namespace splat {
 namespace {
 
+__device__ __forceinline__ float3 f3sub(float3 a, float3 b)
+{
+    return make_float3(a.x - b.x, a.y - b.y, a.z - b.z);
+}
+__device__ __forceinline__ float3 f3cross(float3 a, float3 b)
+{
+    return make_float3(a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x);
+}
+__device__ __forceinline__ float f3dot(float3 a, float3 b)
+{
+    return a.x * b.x + a.y * b.y + a.z * b.z;
+}
+__device__ __forceinline__ float3 f3scale(float3 a, float s)
+{
+    return make_float3(a.x * s, a.y * s, a.z * s);
+}
+
+// One stencil of the self-regularised normal term (Eq. loss_normal with N(D) from the rendered
+// range map, after 2DGS): base pixel u = (r, c), x = (r, c + 1 mod W), y = (r + 1, c);
+// P(w) = D(w) v(w); m = (P(x) - P(u)) x (P(y) - P(u)); n_D = -sign(m . v(u)) m / |m| faces the
+// sensor.  The term lambda (1 - N(u) . n_D) counts where the targets of u, x and y are valid,
+// their rendered ranges are positive and m != 0; the sign is held fixed in the gradient.  Gives
+// the value, n_D and dL/dP at x and y (dL/dP(u) = -(gx + gy)).
+struct Stencil {
+    bool ok;
+    float val;
+    float3 nd, gx, gy;
+};
+
+__device__ __forceinline__ Stencil normal_stencil(const ViewDesc &vd, int r, int c,
+                                                  const float *__restrict__ depth,
+                                                  const float *__restrict__ normal,
+                                                  const float *__restrict__ t_depth, int64_t n,
+                                                  float lambda_n)
+{
+    Stencil s;
+    s.ok = false;
+    if (r < 0 || r + 1 >= vd.rows) return s;
+    const int cx = c + 1 == vd.cols ? 0 : c + 1;
+    const int64_t iu = vd.pixel_offset + static_cast<int64_t>(r) * vd.cols + c;
+    const int64_t ix = iu - c + cx, iy = iu + vd.cols;
+    if (!(t_depth[iu] > 0.0f && t_depth[ix] > 0.0f && t_depth[iy] > 0.0f)) return s;
+    const float du = depth[iu], dxr = depth[ix], dyr = depth[iy];
+    if (!(du > 0.0f && dxr > 0.0f && dyr > 0.0f)) return s;   // a zero range: side undefined
+    const float3 vu = pixel_ray(vd, r, c), vx = pixel_ray(vd, r, cx), vy = pixel_ray(vd, r + 1, c);
+    const float3 pu = f3scale(vu, du);
+    const float3 dx = f3sub(f3scale(vx, dxr), pu), dy = f3sub(f3scale(vy, dyr), pu);
+    const float3 m = f3cross(dx, dy);
+    const float mn = sqrtf(f3dot(m, m));
+    if (!(mn > 0.0f)) return s;
+    const float sgn = f3dot(m, vu) > 0.0f ? -1.0f : 1.0f;
+    const float inv = 1.0f / mn;
+    const float3 mh = f3scale(m, inv);
+    const float3 N = make_float3(normal[iu], normal[n + iu], normal[2 * n + iu]);
+    s.nd = f3scale(mh, sgn);
+    s.val = lambda_n * (1.0f - f3dot(N, s.nd));
+    const float3 g = f3scale(N, -lambda_n);                         // dL/dn_D
+    const float3 gm = f3scale(f3sub(g, f3scale(mh, f3dot(mh, g))), sgn * inv);   // dL/dm
+    s.gx = f3cross(dy, gm);
+    s.gy = f3cross(gm, dx);
+    s.ok = true;
+    return s;
+}
+
+// normal_mode 0: the normal term against the target normals; 1: the self-regularised term
+// (each pixel gathers dL/dD from the three stencils it belongs to, so no atomics are needed).
+template <int kNormalMode>
 __global__ void __launch_bounds__(256) k_loss(const float *__restrict__ depth,
                                               const float *__restrict__ normal,
                                               const float *__restrict__ alpha,
@@ -35,27 +103,47 @@ __global__ void __launch_bounds__(256) k_loss(const float *__restrict__ depth,
          p += static_cast<int64_t>(gridDim.x) * blockDim.x) {
         const float dt = t_depth[p];
         float gd = 0.0f, gn0 = 0.0f, gn1 = 0.0f, gn2 = 0.0f, go = 0.0f;
-        bool use = dt > 0.0f;
-        if (active && use) {   // pixels of views not sampled for this step do not count
-            int v = 0;
+        int v = 0;
+        if (kNormalMode == 1 || active)
             while (v + 1 < n_views && views[v + 1].pixel_offset <= p) ++v;
-            use = active[v] != 0;
-        }
-        if (use) {
+        const bool view_on = !active || active[v] != 0;   // views not sampled do not count
+        if (dt > 0.0f && view_on) {
             const float e = depth[p] - dt;
             acc += fabsf(e);
             gd = e > 0.0f ? 1.0f : (e < 0.0f ? -1.0f : 0.0f);
-            const float n0 = t_normal[p], n1 = t_normal[n + p], n2 = t_normal[2 * n + p];
-            const float dn = normal[p] * n0 + normal[n + p] * n1 + normal[2 * n + p] * n2;
-            acc += lambda_n * (1.0f - dn);
-            gn0 = -lambda_n * n0;
-            gn1 = -lambda_n * n1;
-            gn2 = -lambda_n * n2;
+            if (kNormalMode == 0) {
+                const float n0 = t_normal[p], n1 = t_normal[n + p], n2 = t_normal[2 * n + p];
+                const float dn = normal[p] * n0 + normal[n + p] * n1 + normal[2 * n + p] * n2;
+                acc += lambda_n * (1.0f - dn);
+                gn0 = -lambda_n * n0;
+                gn1 = -lambda_n * n1;
+                gn2 = -lambda_n * n2;
+            }
             if (lambda_o != 0.0f) {
                 const float o = alpha[p];
                 acc += lambda_o * -logf(fmaxf(o, o_eps));
                 go = o > o_eps ? -lambda_o / o : 0.0f;
             }
+        }
+        if (kNormalMode == 1 && view_on && lambda_n != 0.0f) {
+            const ViewDesc &vd = views[v];
+            const int64_t local = p - vd.pixel_offset;
+            const int r = static_cast<int>(local / vd.cols), c = static_cast<int>(local % vd.cols);
+            const float3 vp = pixel_ray(vd, r, c);
+            const Stencil s0 = normal_stencil(vd, r, c, depth, normal, t_depth, n, lambda_n);
+            if (s0.ok) {   // p is the stencil's base u
+                acc += s0.val;
+                gn0 = -lambda_n * s0.nd.x;
+                gn1 = -lambda_n * s0.nd.y;
+                gn2 = -lambda_n * s0.nd.z;
+                gd -= f3dot(make_float3(s0.gx.x + s0.gy.x, s0.gx.y + s0.gy.y, s0.gx.z + s0.gy.z),
+                            vp);
+            }
+            const Stencil s1 = normal_stencil(vd, r, c == 0 ? vd.cols - 1 : c - 1, depth, normal,
+                                              t_depth, n, lambda_n);
+            if (s1.ok) gd += f3dot(s1.gx, vp);   // p is x of its left neighbour's stencil
+            const Stencil s2 = normal_stencil(vd, r - 1, c, depth, normal, t_depth, n, lambda_n);
+            if (s2.ok) gd += f3dot(s2.gy, vp);   // p is y of the stencil above
         }
         g_depth[p] = gd;
         g_normal[p] = gn0;
@@ -168,15 +256,19 @@ cudaError_t launch_loss(const float *depth, const float *normal, const float *al
                         const float *t_depth, const float *t_normal, int64_t n_pixels,
                         float lambda_n, float lambda_o, float o_eps, float *g_depth,
                         float *g_normal, float *g_alpha, double *loss_out, cudaStream_t st,
-                        const ViewDesc *views, int n_views, const uint8_t *active)
+                        const ViewDesc *views, int n_views, const uint8_t *active,
+                        int normal_mode)
 {
     if (n_pixels <= 0) return cudaSuccess;
+    if (normal_mode != 0 && (normal_mode != 1 || !views || n_views < 1))
+        return cudaErrorInvalidValue;
     int64_t blocks = (n_pixels + 255) / 256;
     if (blocks > 4096) blocks = 4096;
-    k_loss<<<static_cast<unsigned>(blocks), 256, 0, st>>>(depth, normal, alpha, t_depth, t_normal,
-                                                          n_pixels, lambda_n, lambda_o, o_eps,
-                                                          g_depth, g_normal, g_alpha, loss_out,
-                                                          views, n_views, active);
+    auto kern = normal_mode == 1 ? k_loss<1> : k_loss<0>;
+    kern<<<static_cast<unsigned>(blocks), 256, 0, st>>>(depth, normal, alpha, t_depth, t_normal,
+                                                        n_pixels, lambda_n, lambda_o, o_eps,
+                                                        g_depth, g_normal, g_alpha, loss_out,
+                                                        views, n_views, active);
     return cudaGetLastError();
 }
 
@@ -260,25 +352,6 @@ cudaError_t launch_backproject(const ViewDesc *views, int n_views, int64_t n_pix
 // keyframe sampling (Sec. 3.3)
 // ---------------------------------------------------------------------------------------------
 namespace {
-
-// Philox-4x32-10 (Salmon, Moraes, Dror, Shaw, SC 2011), from its definition: a round maps
-// (c0, c1, c2, c3) to (hi(M1 c2) ^ c1 ^ k0, lo(M1 c2), hi(M0 c0) ^ c3 ^ k1, lo(M0 c0)); the key
-// is bumped by the Weyl constants between rounds.
-__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k)
-{
-    constexpr uint32_t M0 = 0xD2511F53u, M1 = 0xCD9E8D57u, W0 = 0x9E3779B9u, W1 = 0xBB67AE85u;
-#pragma unroll
-    for (int r = 0; r < 10; ++r) {
-        const uint32_t hi0 = __umulhi(M0, c.x), lo0 = M0 * c.x;
-        const uint32_t hi1 = __umulhi(M1, c.z), lo1 = M1 * c.z;
-        c = make_uint4(hi1 ^ c.y ^ k.x, lo1, hi0 ^ c.w ^ k.y, lo0);
-        if (r < 9) {
-            k.x += W0;
-            k.y += W1;
-        }
-    }
-    return c;
-}
 
 __global__ void k_sample_views(int n_views, int draws, const uint32_t *__restrict__ thr,
                                uint32_t seed_lo, uint32_t seed_hi, uint32_t *__restrict__ step,

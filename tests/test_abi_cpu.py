@@ -73,3 +73,21 @@ def test_no_graphics_or_fallback_imports():
             if f.endswith(".py"):
                 src = open(os.path.join(dirpath, f)).read()
                 assert "import oracle" not in src and "from oracle" not in src, f
+
+
+def _prototypes():
+    """name -> parameter count of every SPLAT_API prototype in the header."""
+    text = re.sub(r"/\*.*?\*/", "", open(HEADER).read(), flags=re.S)
+    out = {}
+    for m in re.finditer(r"SPLAT_API\s+[\w\s\*]+?\b(splat_\w+)\s*\(([^)]*)\)\s*;", text):
+        args = m.group(2).strip()
+        out[m.group(1)] = 0 if args in ("", "void") else args.count(",") + 1
+    return out
+
+
+def test_binding_arity_matches_the_header():
+    from paper_2503_17491_gb300 import _lib
+    protos = _prototypes()
+    assert sorted(protos) == declared()
+    for name, (argtypes, _) in _lib.SIGNATURES.items():
+        assert len(argtypes) == protos[name], (name, len(argtypes), protos[name])
