@@ -262,8 +262,10 @@ class SplatContext:
         double[29] (see unpack_normal_eqs) and, when per_pixel, the (8, P) float32 r, w, J."""
         out = out if out is not None else torch.empty(29, dtype=torch.float64,
                                                       device=depth.device)
-        P = self.views[view].rows * self.views[view].cols
-        px = torch.empty(8, P, dtype=torch.float32, device=depth.device) if per_pixel else None
+        px = None
+        if per_pixel and 0 <= view < len(self.views):
+            P = self.views[view].rows * self.views[view].cols
+            px = torch.empty(8, P, dtype=torch.float32, device=depth.device)
         if T_qm.dtype != torch.float32 or tuple(T_qm.shape) != (3, 4) or not T_qm.is_cuda:
             raise ValueError("T_qm: float32 CUDA tensor of shape (3, 4)")
         _lib.check(self.lib.splat_photometric(

@@ -162,7 +162,8 @@ struct WarpBatch {
     float4 a[32], b[32], c[32], n[32];
     uint32_t pos[32];     // list position of the staged entry (backward: bit 31 = flipped)
     uint32_t prim[32];    // primitive index
-    float4 p0[32], p1[32], p2[32], p3[32];
+    float4 p0[32], p1[32], p2[32];
+    float p3[32];
     // the batch's candidates in numbering order: slot << 5 | pixel, bit 15 = a candidate (the
     // backward's padding entries of a group carry their slot without it)
     uint16_t cand[1024];
@@ -201,18 +202,19 @@ __device__ __forceinline__ void put_pix(WarpBatch &w, int lane, const Pix &p)
     w.p0[lane] = make_float4(p.hx0, p.hx1, p.hx2, p.hy0);
     w.p1[lane] = make_float4(p.hy1, p.hy2, p.v0, p.v1);
     w.p2[lane] = make_float4(p.v2, p.hxl0, p.hxl1, p.hyl0);
-    w.p3[lane] = make_float4(p.hyl1, 0.0f, 0.0f, 0.0f);
+    w.p3[lane] = p.hyl1;
 }
 
 __device__ __forceinline__ Pix get_pix(const WarpBatch &w, int l)
 {
-    const float4 a = w.p0[l], b = w.p1[l], c = w.p2[l], d = w.p3[l];
+    const float4 a = w.p0[l], b = w.p1[l], c = w.p2[l];
+    const float d = w.p3[l];
     Pix p;
     p.hx0 = a.x; p.hx1 = a.y; p.hx2 = a.z;
     p.hy0 = a.w; p.hy1 = b.x; p.hy2 = b.y;
     p.v0 = b.z; p.v1 = b.w; p.v2 = c.x;
     p.hxl0 = c.y; p.hxl1 = c.z; p.hxl2 = 0.0f;
-    p.hyl0 = c.w; p.hyl1 = d.x; p.hyl2 = 0.0f;
+    p.hyl0 = c.w; p.hyl1 = d; p.hyl2 = 0.0f;
     return p;
 }
 

@@ -70,7 +70,8 @@ def test_photometric_parity_on_a_rendered_view():
 
 def test_gauss_newton_on_the_gpu_recovers_a_known_pose():
     """Ray-cast model and query scans (exact ranges): Gauss-Newton steps with the GPU's normal
-    equations, the pose update on the host, bring a 0.15 m / 1 degree offset down five-fold."""
+    equations, the pose update on the host, bring a 0.15 m / 1 degree offset down five-fold (the
+    oracle's own iteration on these images needs ten steps for that)."""
     s, vm, Dq, T_true = _setup(n=1000)
     D = scenes.render_targets(s, vm, noise=0.0)[0].ravel().astype(np.float32)
     O = (D > 0).astype(np.float32)
@@ -83,7 +84,7 @@ def test_gauss_newton_on_the_gpu_recovers_a_known_pose():
         return np.linalg.norm(E[:3, 3]), math.acos(max(-1.0, min(1.0, (np.trace(E[:3, :3]) - 1) / 2)))
 
     e0 = err(T)
-    for _ in range(8):
+    for _ in range(11):
         H, g, cost, count = api.unpack_normal_eqs(ctx.photometric(0, Dt, Ot, Qt, _t34(T), 0.5, 0.3))
         T = T @ se3_exp(-np.linalg.solve(H + 1e-9 * np.eye(6), g))
     e1 = err(T)
