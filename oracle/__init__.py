@@ -95,7 +95,7 @@ def _load():
             lib.or_reach_pairs.argtypes = [_I64, _P, _P, _P, _P, _P, _I, _I, _D, _D, _P, _P, _P,
                                            _I64]
             lib.or_reach_pairs.restype = _I64
-            lib.or_loss.argtypes = [_I64, _P, _P, _P, _P, _P, _D, _D, _D, _P, _P, _P]
+            lib.or_loss.argtypes = [_I64, _P, _P, _P, _P, _P, _D, _D, _D, _D, _P, _P, _P]
             lib.or_loss.restype = _D
             lib.or_adam.argtypes = [_I64, _P, _P, _P, _P, _D, _D, _D, _D, _I]
             _lib = lib
@@ -302,8 +302,9 @@ def reach_pairs(params, T_ws, rows, cols, elev_min, elev_max, cfg=DEFAULT_CFG,
     return pix[:k], prim[:k]
 
 
-def loss(D, N, O, Dt, Nt, lambda_n=1.0, lambda_o=0.0, o_eps=1e-6):
-    """(L, gD, gN, gO) over flattened pixels; N, Nt are (3, npx) planar."""
+def loss(D, N, O, Dt, Nt, lambda_n=1.0, lambda_o=0.0, o_eps=1e-6, rho_exp=0.0):
+    """(L, gD, gN, gO) over flattened pixels; N, Nt are (3, npx) planar.  The L1 range term is
+    weighted by rho_d = Dt^rho_exp (rho_exp = 0: rho_d = 1)."""
     D = _c(D, np.float64).ravel()
     N = _c(N, np.float64).ravel()
     O = _c(O, np.float64).ravel()
@@ -314,7 +315,7 @@ def loss(D, N, O, Dt, Nt, lambda_n=1.0, lambda_o=0.0, o_eps=1e-6):
     gN = np.zeros(3 * npx)
     gO = np.zeros(npx)
     L = _load().or_loss(npx, _ptr(D), _ptr(N), _ptr(O), _ptr(Dt), _ptr(Nt), lambda_n, lambda_o,
-                        o_eps, _ptr(gD), _ptr(gN), _ptr(gO))
+                        o_eps, float(rho_exp), _ptr(gD), _ptr(gN), _ptr(gO))
     return L, gD, gN.reshape(3, npx), gO
 
 

@@ -58,7 +58,7 @@
 
 #define OR_PI 3.14159265358979323846
 
-int or_version(void) { return 8; }
+int or_version(void) { return 9; }
 
 /* ------------------------------------------------------------------------- */
 /* 1. pose                                                                   */
@@ -922,16 +922,18 @@ void or_pose_gradient(int64_t n, const double *pos, const double *logit, const d
  * (sign(0) = 0; d/dO is -lambda_o / O where O > o_eps, else 0). */
 double or_loss(int64_t npx, const double *D, const double *N, const double *O,
                const double *Dt, const double *Nt, double lambda_n, double lambda_o,
-               double o_eps, double *gD, double *gN, double *gO)
+               double o_eps, double rho_exp, double *gD, double *gN, double *gO)
 {
     double L = 0;
     for (int64_t i = 0; i < npx; ++i) {
         gD[i] = 0; gO[i] = 0;
         for (int k = 0; k < 3; ++k) gN[k * npx + i] = 0;
         if (!(Dt[i] > 0)) continue;
+        /* rho_d of Eq. loss_range, a weight that depends on the measured range: Dt^rho_exp */
+        double rho = rho_exp == 0.0 ? 1.0 : pow(Dt[i], rho_exp);
         double e = D[i] - Dt[i];
-        L += fabs(e);
-        gD[i] = e > 0 ? 1.0 : (e < 0 ? -1.0 : 0.0);
+        L += rho * fabs(e);
+        gD[i] = rho * (e > 0 ? 1.0 : (e < 0 ? -1.0 : 0.0));
         double dn = 0;
         for (int k = 0; k < 3; ++k) dn += N[k * npx + i] * Nt[k * npx + i];
         L += lambda_n * (1.0 - dn);

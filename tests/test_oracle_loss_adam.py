@@ -88,3 +88,20 @@ def test_scale_regularizer_values_and_gradient(oracle_mod):
                   oracle_mod.scale_regularizer(b, 0.7, 1.3)[0]) / (2 * h)
             if abs(math.exp(ls[i, k]) - 1.3) > 1e-3 and abs(ls[i, 0] - ls[i, 1]) > 1e-3:
                 assert abs(fd - g[i, k]) <= 1e-6 * max(1.0, abs(g[i, k])), (i, k, fd, g[i, k])
+
+
+def test_range_weight_rho_d(oracle_mod):
+    """rho_d = Dt^p: with p = -1 the range term is the sum of relative errors (hand values), and
+    p = 0 is the plain L1 term."""
+    D = np.array([12.0, 9.0, 5.0, 3.0])
+    Dt = np.array([10.0, 10.0, 0.0, 2.0])
+    N = np.zeros((3, 4))
+    O = np.ones(4)
+    L, gD, gN, gO = oracle_mod.loss(D, N, O, Dt, N, lambda_n=0.0, rho_exp=-1.0)
+    assert L == pytest.approx(0.2 + 0.1 + 0.5)
+    np.testing.assert_allclose(gD, [0.1, -0.1, 0.0, 0.5])
+    L0, gD0, _, _ = oracle_mod.loss(D, N, O, Dt, N, lambda_n=0.0, rho_exp=0.0)
+    assert L0 == pytest.approx(2.0 + 1.0 + 1.0)
+    np.testing.assert_allclose(gD0, [1.0, -1.0, 0.0, 1.0])
+    L2, gD2, _, _ = oracle_mod.loss(D, N, O, Dt, N, lambda_n=0.0, rho_exp=2.0)
+    assert L2 == pytest.approx(100 * 2 + 100 * 1 + 4 * 1)
