@@ -109,9 +109,11 @@ typedef struct {
     int64_t max_tiles;
 } splat_capacity;
 
-/* Loss weights of Eq. loss_full (rho_d = 1): o_eps floors O inside -log O.  lambda_s and tau_s
- * weigh the scale term of splat_refine_step, lambda_s sum_i max(0, max(s_a, s_b)_i - tau_s) (the
- * penalty of Eq. L_s with its sign read as growth beyond tau_s; 0 disables it).
+/* Loss weights of Eq. loss_full: o_eps floors O inside -log O; rho_d of Eq. loss_range, a
+ * weight that depends on the measured range and has no printed form, is read as Dt^rho_exp.
+ * lambda_s and tau_s weigh the scale term of splat_refine_step, lambda_s sum_i max(0,
+ * max(s_a, s_b)_i - tau_s) (the penalty of Eq. L_s with its sign read as growth beyond tau_s; 0
+ * disables it).
  * normal_mode selects the normal term of Eq. loss_normal:
  *   SPLAT_NORMALS_TARGET (0): lambda_n (1 - N(u) . Nt(u)) against the target normals;
  *   SPLAT_NORMALS_RANGE_MAP (1): self-regularised, lambda_n (1 - N(u) . n_D(u)) with n_D the
@@ -127,6 +129,7 @@ typedef struct {
     float lambda_n, lambda_o, o_eps;
     float lambda_s, tau_s;
     int32_t normal_mode;
+    float rho_exp;            /* rho_d = target_depth^rho_exp weighs the L1 range term (0: 1) */
 } splat_loss_config;
 
 /* Map growth (Sec. 3.3.1 local model initialisation, Sec. 3.3.2 densification).
@@ -319,8 +322,8 @@ SPLAT_API int splat_photometric(splat_ctx *ctx, int32_t view, const float *depth
 
 /* Per-pixel loss over n_pixels packed pixels (depth/alpha/target_depth [P], normal and
  * target_normal [3][P] planar with plane stride n_pixels): valid pixels are those with
- * target_depth > 0 (M_v); L = sum |D - Dt| + lambda_n (1 - N . Nt) + lambda_o (-log max(O,
- * o_eps)).  Writes dL_ddepth, dL_dnormal (3 x P), dL_dalpha (0 outside M_v), and ADDS L to
+ * target_depth > 0 (M_v); L = sum Dt^rho_exp |D - Dt| + lambda_n (1 - N . Nt) + lambda_o (-log
+ * max(O, o_eps)).  Writes dL_ddepth, dL_dnormal (3 x P), dL_dalpha (0 outside M_v), and ADDS L to
  * *loss_out (device double; caller zeroes it).  cfg->normal_mode must be SPLAT_NORMALS_TARGET
  * (the range-map mode needs the views: splat_view_loss).  Errors: INVALID_ARG, CUDA. */
 SPLAT_API int splat_loss(const float *depth, const float *normal, const float *alpha,

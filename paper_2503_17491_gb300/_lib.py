@@ -41,7 +41,8 @@ class splat_capacity(ctypes.Structure):
 class splat_loss_config(ctypes.Structure):
     _fields_ = [("lambda_n", ctypes.c_float), ("lambda_o", ctypes.c_float),
                 ("o_eps", ctypes.c_float), ("lambda_s", ctypes.c_float),
-                ("tau_s", ctypes.c_float), ("normal_mode", ctypes.c_int32)]
+                ("tau_s", ctypes.c_float), ("normal_mode", ctypes.c_int32),
+                ("rho_exp", ctypes.c_float)]
 
 
 class splat_densify_config(ctypes.Structure):

@@ -79,10 +79,11 @@ class LossConfig:
     lambda_s: float = 0.0   # scale term (splat_refine_step only)
     tau_s: float = 0.5
     normal_mode: int = 0    # 0: against target normals; 1: normals of the rendered range map
+    rho_exp: float = 0.0    # range weight rho_d = Dt^rho_exp of the L1 term
 
     def c(self):
         return _lib.splat_loss_config(self.lambda_n, self.lambda_o, self.o_eps, self.lambda_s,
-                                      self.tau_s, self.normal_mode)
+                                      self.tau_s, self.normal_mode, self.rho_exp)
 
 
 @dataclass

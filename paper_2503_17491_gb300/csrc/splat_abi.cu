@@ -736,7 +736,7 @@ SPLAT_API int splat_loss(const float *depth, const float *normal, const float *a
         cfg->normal_mode != SPLAT_NORMALS_TARGET)
         return SPLAT_ERR_INVALID_ARG;
     CK(splat::launch_loss(depth, normal, alpha, target_depth, target_normal, n_pixels,
-                          cfg->lambda_n, cfg->lambda_o, cfg->o_eps, dL_ddepth, dL_dnormal,
+                          cfg->lambda_n, cfg->lambda_o, cfg->o_eps, cfg->rho_exp, dL_ddepth, dL_dnormal,
                           dL_dalpha, loss_out, static_cast<cudaStream_t>(stream)));
     return SPLAT_OK;
 }
@@ -758,7 +758,7 @@ SPLAT_API int splat_view_loss(splat_ctx *ctx, const float *depth, const float *n
         return SPLAT_ERR_INVALID_ARG;
     if (ctx->n_views < 1) return SPLAT_ERR_STATE;
     CK(splat::launch_loss(depth, normal, alpha, target_depth, target_normal, ctx->n_pixels,
-                          cfg->lambda_n, cfg->lambda_o, cfg->o_eps, dL_ddepth, dL_dnormal,
+                          cfg->lambda_n, cfg->lambda_o, cfg->o_eps, cfg->rho_exp, dL_ddepth, dL_dnormal,
                           dL_dalpha, loss_out, static_cast<cudaStream_t>(stream), ctx->d_views,
                           ctx->n_views, nullptr, cfg->normal_mode));
     return SPLAT_OK;
@@ -826,7 +826,8 @@ SPLAT_API int splat_refine_step(splat_ctx *ctx, float *pos_logit, float *quat, f
     if (r) return r;
     CK(cudaMemsetAsync(loss_out, 0, sizeof(double), st));
     CK(splat::launch_loss(depth, normal, alpha, target_depth, target_normal, P, loss_cfg->lambda_n,
-                          loss_cfg->lambda_o, loss_cfg->o_eps, gd, gn, ga, loss_out, st,
+                          loss_cfg->lambda_o, loss_cfg->o_eps, loss_cfg->rho_exp, gd, gn, ga,
+                          loss_out, st,
                           ctx->d_views, ctx->n_views,
                           ctx->samp_draws > 0 ? ctx->d_active : nullptr,
                           loss_cfg->normal_mode));

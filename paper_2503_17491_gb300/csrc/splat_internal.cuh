@@ -449,9 +449,9 @@ cudaError_t launch_param_grads(const float4 *pos_logit, const float4 *quat, cons
 // self-regularised against the normals of the rendered range map (needs views; t_normal unused)
 cudaError_t launch_loss(const float *depth, const float *normal, const float *alpha,
                         const float *t_depth, const float *t_normal, int64_t n_pixels,
-                        float lambda_n, float lambda_o, float o_eps, float *g_depth,
-                        float *g_normal, float *g_alpha, double *loss_out, cudaStream_t st,
-                        const ViewDesc *views = nullptr, int n_views = 0,
+                        float lambda_n, float lambda_o, float o_eps, float rho_exp,
+                        float *g_depth, float *g_normal, float *g_alpha, double *loss_out,
+                        cudaStream_t st, const ViewDesc *views = nullptr, int n_views = 0,
                         const uint8_t *active = nullptr, int normal_mode = 0);
 
 struct AdamArgs {

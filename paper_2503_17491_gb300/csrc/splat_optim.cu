@@ -1,7 +1,7 @@
 // K8 (loss) and K9 (Adam, optionally fused with K7).
 //
 // Loss over the valid pixels M_v (target range > 0, Sec. 3.3.1): the L1 range term of
-// Eq. loss_range (rho_d = 1), the normal term of Eq. loss_normal taken either against the target
+// Eq. loss_range (rho_d = Dt^rho_exp, 1 by default), the normal term of Eq. loss_normal taken either against the target
 // normal or against the normal of the rendered range map (self-regularised), and optionally the
 // opacity term of Eq. loss_opacity.  Per-pixel gradients are written
 // for the backward; the scalar is reduced per warp in binary32 and per CTA in binary64.
@@ -90,7 +90,7 @@ __global__ void __launch_bounds__(256) k_loss(const float *__restrict__ depth,
                                               const float *__restrict__ t_depth,
                                               const float *__restrict__ t_normal, int64_t n,
                                               float lambda_n, float lambda_o, float o_eps,
-                                              float *__restrict__ g_depth,
+                                              float rho_exp, float *__restrict__ g_depth,
                                               float *__restrict__ g_normal,
                                               float *__restrict__ g_alpha,
                                               double *__restrict__ loss_out,
@@ -108,9 +108,10 @@ __global__ void __launch_bounds__(256) k_loss(const float *__restrict__ depth,
             while (v + 1 < n_views && views[v + 1].pixel_offset <= p) ++v;
         const bool view_on = !active || active[v] != 0;   // views not sampled do not count
         if (dt > 0.0f && view_on) {
+            const float rho = rho_exp == 0.0f ? 1.0f : powf(dt, rho_exp);   // rho_d = Dt^p
             const float e = depth[p] - dt;
-            acc += fabsf(e);
-            gd = e > 0.0f ? 1.0f : (e < 0.0f ? -1.0f : 0.0f);
+            acc += rho * fabsf(e);
+            gd = e > 0.0f ? rho : (e < 0.0f ? -rho : 0.0f);
             if (kNormalMode == 0) {
                 const float n0 = t_normal[p], n1 = t_normal[n + p], n2 = t_normal[2 * n + p];
                 const float dn = normal[p] * n0 + normal[n + p] * n1 + normal[2 * n + p] * n2;
@@ -254,10 +255,10 @@ __global__ void k_step_inc(int32_t *step)
 
 cudaError_t launch_loss(const float *depth, const float *normal, const float *alpha,
                         const float *t_depth, const float *t_normal, int64_t n_pixels,
-                        float lambda_n, float lambda_o, float o_eps, float *g_depth,
-                        float *g_normal, float *g_alpha, double *loss_out, cudaStream_t st,
-                        const ViewDesc *views, int n_views, const uint8_t *active,
-                        int normal_mode)
+                        float lambda_n, float lambda_o, float o_eps, float rho_exp,
+                        float *g_depth, float *g_normal, float *g_alpha, double *loss_out,
+                        cudaStream_t st, const ViewDesc *views, int n_views,
+                        const uint8_t *active, int normal_mode)
 {
     if (n_pixels <= 0) return cudaSuccess;
     if (normal_mode != 0 && (normal_mode != 1 || !views || n_views < 1))
@@ -267,7 +268,8 @@ cudaError_t launch_loss(const float *depth, const float *normal, const float *al
     auto kern = normal_mode == 1 ? k_loss<1> : k_loss<0>;
     kern<<<static_cast<unsigned>(blocks), 256, 0, st>>>(depth, normal, alpha, t_depth, t_normal,
                                                         n_pixels, lambda_n, lambda_o, o_eps,
-                                                        g_depth, g_normal, g_alpha, loss_out,
+                                                        rho_exp, g_depth, g_normal, g_alpha,
+                                                        loss_out,
                                                         views, n_views, active);
     return cudaGetLastError();
 }

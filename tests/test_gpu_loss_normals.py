@@ -112,3 +112,21 @@ def test_refine_step_range_map_normals():
         ls.append(float(loss_out.item()))
     assert ls[0] == pytest.approx(L0, rel=1e-5)
     assert ls[-1] < ls[0]
+
+
+@pytest.mark.parametrize("p", [-1.0, 0.5])
+def test_range_weight_parity(p):
+    """rho_d = Dt^p on the L1 range term, context-free splat_loss against the oracle."""
+    rng = np.random.default_rng(12)
+    P = 6000
+    D = rng.uniform(0, 60, P).astype(np.float32)
+    N = rng.normal(size=(3, P)).astype(np.float32)
+    O = rng.uniform(0, 1, P).astype(np.float32)
+    Dt = np.where(rng.uniform(size=P) < 0.2, 0, rng.uniform(0.5, 60, P)).astype(np.float32)
+    Nt = rng.normal(size=(3, P)).astype(np.float32)
+    cfg = api.LossConfig(lambda_n=0.3, lambda_o=0.05, rho_exp=p)
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()  # noqa: E731
+    L, gD, gN, gO = api.loss(t(D), t(N), t(O), t(Dt), t(Nt), cfg)
+    Lr, gDr, gNr, gOr = oracle.loss(D, N, O, Dt, Nt, 0.3, 0.05, 1e-6, rho_exp=p)
+    assert float(L) == pytest.approx(Lr, rel=1e-5)
+    np.testing.assert_allclose(gD.cpu().numpy(), gDr, rtol=2e-6, atol=1e-7)
