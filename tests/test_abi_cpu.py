@@ -91,3 +91,20 @@ def test_binding_arity_matches_the_header():
     assert sorted(protos) == declared()
     for name, (argtypes, _) in _lib.SIGNATURES.items():
         assert len(argtypes) == protos[name], (name, len(argtypes), protos[name])
+
+
+def test_argument_checks_of_the_map_and_tracking_calls(lib):
+    """splat_view_loss, splat_densify and splat_photometric reject null arguments before any
+    device work (status 1 = INVALID_ARG)."""
+    from paper_2503_17491_gb300 import _lib
+    cfg = _lib.splat_loss_config(1.0, 0.0, 1e-6, 0.0, 0.5, 1, 0.0)
+    assert lib.splat_view_loss(None, None, None, None, None, None, ctypes.byref(cfg), None, None,
+                               None, None, None) == 1
+    dcfg = _lib.splat_densify_config(0, 0.5, 0.1, 0.05, 2.0, 2.0, 0.5, 0)
+    assert lib.splat_densify(None, None, None, None, ctypes.byref(dcfg), 10, None, None, None, 0,
+                             10, None) == 1
+    assert lib.splat_photometric(None, 0, None, None, None, None, 0.5, 0.2, None, None,
+                                 None) == 1
+    # the context-free loss has no view geometry for the range-map normal mode
+    assert lib.splat_loss(None, None, None, None, None, 0, ctypes.byref(cfg), None, None, None,
+                          None, None) == 1
