@@ -241,10 +241,11 @@ def cpu_baseline(scene, views, targets, budget_s, seed=0):
                                v.elev_max, gD, gN, gO, culled=cul, pixels=px)
         return time.perf_counter() - t
 
-    probe = 256
-    tp = run(probe)
-    k = int(max(probe, min(1 << 20, probe * budget_s / max(tp, 1e-6))))
-    t = run(k)
+    # grow the sample until it takes about the budget (a small run is dominated by fixed costs)
+    k, t = 256, run(256)
+    while t < 0.5 * budget_s and k < (1 << 20):
+        k = int(min(1 << 20, max(2 * k, 0.9 * k * budget_s / max(t, 1e-6))))
+        t = run(k)
     return {"value": k / t, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
             "sample": (f"FP64 oracle forward + loss + backward of {k} random pixels of keyframe "
                        f"{vi} ({v.rows}x{v.cols}) of the same workload, culled mode, OpenMP on all "
