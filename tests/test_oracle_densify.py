@@ -152,3 +152,23 @@ def test_normal_straight_down_uses_the_fallback_rotation():
     T = np.eye(4)
     pl, q, ls = oracle.init_primitive(5.0, np.array([0.0, 0.0, 1.0]), T, 0.01, 0.01, 1.0, 0.5)
     np.testing.assert_allclose(_quat_rot(q)[:, 2], [0, 0, -1], atol=1e-15)
+
+
+def test_invalid_lower_neighbour_gives_no_vertical_gradient():
+    """A ray drop below a valid pixel contributes no range gradient (it is not a surface edge)."""
+    rows, cols = 6, 20
+    Dt = np.full((rows, cols), 10.0, np.float32)
+    Dt[3, 5] = 0.0
+    q = oracle.densify_weights(Dt, None, None, rows, cols, False, 0, 0, 0.25, 16.0)
+    q = q.reshape(rows, cols).astype(np.int64)
+    assert q[2, 5] == 64 and q[3, 4] == 64 and q[3, 5] == 0
+
+
+def test_offset_is_one_quantile_of_every_total():
+    """The draw's offset is the quantile x / 2^32 of the total weight: doubling the total doubles
+    the offset (up to the floor), whatever the call."""
+    for call in range(50):
+        for Q in (1000, 77777, 123456789):
+            o1 = oracle.densify_offset(Q, 5, call)
+            o2 = oracle.densify_offset(2 * Q, 5, call)
+            assert o2 in (2 * o1, 2 * o1 + 1)
