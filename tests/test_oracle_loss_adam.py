@@ -105,3 +105,15 @@ def test_range_weight_rho_d(oracle_mod):
     np.testing.assert_allclose(gD0, [1.0, -1.0, 0.0, 1.0])
     L2, gD2, _, _ = oracle_mod.loss(D, N, O, Dt, N, lambda_n=0.0, rho_exp=2.0)
     assert L2 == pytest.approx(100 * 2 + 100 * 1 + 4 * 1)
+
+
+def test_opacity_term_is_flat_below_its_floor(oracle_mod):
+    """-log max(O, o_eps) is constant for O below o_eps, so its gradient is zero there, and
+    the value is -log o_eps (hand values)."""
+    D = np.array([1.0, 1.0])
+    Dt = np.array([1.0, 1.0])
+    Z = np.zeros((3, 2))
+    O = np.array([1e-8, 0.5])
+    L, gD, gN, gO = oracle_mod.loss(D, Z, O, Dt, Z, lambda_n=0.0, lambda_o=2.0, o_eps=1e-6)
+    assert L == pytest.approx(2.0 * (-math.log(1e-6) - math.log(0.5)))
+    np.testing.assert_allclose(gO, [0.0, -4.0])
