@@ -197,3 +197,20 @@ def test_sorted_keys_and_ranges(oracle_mod):
     nonempty = end > start
     assert (end - start)[nonempty].sum() == len(keys)
     assert np.all(tiles[start[nonempty]] == np.nonzero(nonempty)[0])
+
+
+@pytest.mark.parametrize("o,bound", [(2.0 / 255.0, "reach"), (0.9, "box")])
+def test_bbox_is_clipped_to_the_contributing_region(oracle_mod, o, bound):
+    """A head-on splat at 5 m (t_a = y, t_b = z, 0.3 m scales): its columns span the angle where
+    it can contribute, |s| <= a with a = min(sigma, r_o), r_o = sqrt(2 ln(o / alpha_min)) -- for
+    o = 2 alpha_min that is r_o = 1.18 of the 3-sigma box, not the box (closed form, with the
+    contract's small margins)."""
+    v = scenes.View(np.eye(4), 33, 512, scenes.deg(-16), scenes.deg(16))
+    d, s = 5.0, 0.3
+    pl, q, ls = _single((d, 0.0, 0.0), (0.5, 0.5, 0.5, 0.5), (s, s), o=o)
+    proj, pix, prim = _check_coverage(oracle_mod, pl, q, ls, v, min_pairs=10)
+    a = min(3.0, math.sqrt(2.0 * math.log(o * 255.0))) if bound == "reach" else 3.0
+    dg = 2 * math.pi / v.cols
+    half = math.atan(a * s / d) / dg               # columns each side of the centre
+    nc = int(proj["pix_rect"][0][3])
+    assert 2 * half - 1 <= nc <= 2 * half * 1.003 + 3, (nc, half)
