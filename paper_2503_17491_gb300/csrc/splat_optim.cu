@@ -46,7 +46,37 @@ struct Stencil {
     float3 nd, gx, gy;
 };
 
+// The pixel-centre rays of the 3 x 3 neighbourhood of pixel (r, c) (columns wrapped), from one
+// sine/cosine pair per row and per column: ray(i, j) is the ray of (r - 1 + i, c - 1 + j), the
+// same products pixel_ray forms.
+struct Rays3x3 {
+    float ct[3], st[3], cg[3], sg[3];
+    __device__ __forceinline__ float3 ray(int i, int j) const
+    {
+        return make_float3(ct[i] * cg[j], ct[i] * sg[j], st[i]);
+    }
+};
+
+__device__ __forceinline__ Rays3x3 rays_around(const ViewDesc &vd, int r, int c)
+{
+    Rays3x3 t;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        const int rr = r - 1 + i;
+        const float th = vd.rows > 1 ? vd.elev_max - vd.dtheta * static_cast<float>(rr)
+                                     : vd.elev_max;
+        sincosf(th, &t.st[i], &t.ct[i]);
+        int cc = c - 1 + i;
+        cc = cc < 0 ? cc + vd.cols : (cc >= vd.cols ? cc - vd.cols : cc);
+        const float g = 3.14159265358979f - vd.dgamma * (static_cast<float>(cc) + 0.5f);
+        sincosf(g, &t.sg[i], &t.cg[i]);
+    }
+    return t;
+}
+
+// the stencil with base (r, c) = neighbourhood offset (i, j) of the rays' centre pixel
 __device__ __forceinline__ Stencil normal_stencil(const ViewDesc &vd, int r, int c,
+                                                  const Rays3x3 &rays, int i, int j,
                                                   const float *__restrict__ depth,
                                                   const float *__restrict__ normal,
                                                   const float *__restrict__ t_depth, int64_t n,
@@ -61,7 +91,7 @@ __device__ __forceinline__ Stencil normal_stencil(const ViewDesc &vd, int r, int
     if (!(t_depth[iu] > 0.0f && t_depth[ix] > 0.0f && t_depth[iy] > 0.0f)) return s;
     const float du = depth[iu], dxr = depth[ix], dyr = depth[iy];
     if (!(du > 0.0f && dxr > 0.0f && dyr > 0.0f)) return s;   // a zero range: side undefined
-    const float3 vu = pixel_ray(vd, r, c), vx = pixel_ray(vd, r, cx), vy = pixel_ray(vd, r + 1, c);
+    const float3 vu = rays.ray(i, j), vx = rays.ray(i, j + 1), vy = rays.ray(i + 1, j);
     const float3 pu = f3scale(vu, du);
     const float3 dx = f3sub(f3scale(vx, dxr), pu), dy = f3sub(f3scale(vy, dyr), pu);
     const float3 m = f3cross(dx, dy);
@@ -130,8 +160,10 @@ __global__ void __launch_bounds__(256) k_loss(const float *__restrict__ depth,
             const ViewDesc &vd = views[v];
             const int64_t local = p - vd.pixel_offset;
             const int r = static_cast<int>(local / vd.cols), c = static_cast<int>(local % vd.cols);
-            const float3 vp = pixel_ray(vd, r, c);
-            const Stencil s0 = normal_stencil(vd, r, c, depth, normal, t_depth, n, lambda_n);
+            const Rays3x3 rays = rays_around(vd, r, c);
+            const float3 vp = rays.ray(1, 1);
+            const Stencil s0 = normal_stencil(vd, r, c, rays, 1, 1, depth, normal, t_depth, n,
+                                              lambda_n);
             if (s0.ok) {   // p is the stencil's base u
                 acc += s0.val;
                 gn0 = -lambda_n * s0.nd.x;
@@ -140,10 +172,11 @@ __global__ void __launch_bounds__(256) k_loss(const float *__restrict__ depth,
                 gd -= f3dot(make_float3(s0.gx.x + s0.gy.x, s0.gx.y + s0.gy.y, s0.gx.z + s0.gy.z),
                             vp);
             }
-            const Stencil s1 = normal_stencil(vd, r, c == 0 ? vd.cols - 1 : c - 1, depth, normal,
-                                              t_depth, n, lambda_n);
+            const Stencil s1 = normal_stencil(vd, r, c == 0 ? vd.cols - 1 : c - 1, rays, 1, 0,
+                                              depth, normal, t_depth, n, lambda_n);
             if (s1.ok) gd += f3dot(s1.gx, vp);   // p is x of its left neighbour's stencil
-            const Stencil s2 = normal_stencil(vd, r - 1, c, depth, normal, t_depth, n, lambda_n);
+            const Stencil s2 = normal_stencil(vd, r - 1, c, rays, 0, 1, depth, normal, t_depth, n,
+                                              lambda_n);
             if (s2.ok) gd += f3dot(s2.gy, vp);   // p is y of the stencil above
         }
         g_depth[p] = gd;
