@@ -542,3 +542,82 @@ def autotune_tile(params, views, targets, shapes=TILE_SHAPES, steps=3, max_pairs
     best = min(times, key=times.get)
     th, tw = (int(x) for x in best.split("x"))
     return (th, tw), times
+
+
+class Mapper:
+    """The local-model loop of Sec. 3.3 on one shared map, built from the library's calls:
+    each new keyframe is registered, the map grows from it (splat_densify: the valid mask for the
+    first keyframe, the densification masks M_n / M_e against a render of the current map for
+    later ones), then refinement iterations (splat_refine_step) run over the registered keyframes
+    with keyframe sampling (splat_set_view_sampling).  The parameters and Adam moments live in
+    tensors of a fixed capacity; the first `n` rows are the map."""
+
+    def __init__(self, capacity: int, max_views: int, max_pixels: int, n_new: int,
+                 cfg: RenderConfig | None = None, loss_cfg: LossConfig | None = None,
+                 adam_cfg: AdamConfig | None = None, densify_cfg: DensifyConfig | None = None,
+                 draws: int = 2, p_newest: float = 0.4, seed: int = 0, device="cuda"):
+        self.capacity, self.n_new = int(capacity), int(n_new)
+        self.draws, self.p_newest, self.seed = int(draws), float(p_newest), int(seed)
+        self.loss_cfg = loss_cfg or LossConfig(lambda_n=0.1, normal_mode=1)
+        self.adam_cfg = adam_cfg or AdamConfig()
+        self.densify_cfg = densify_cfg or DensifyConfig()
+        dev = torch.device(device)
+        self.ctx = SplatContext(self.capacity, max_views, max_pixels, None, cfg)
+        self.params = [torch.zeros(self.capacity, w, device=dev) for w in (4, 4, 2)]
+        self.state = adam_state(self.capacity, dev)
+        self.n = 0
+        self.views: list = []
+        self.t_depth = torch.zeros(0, device=dev)
+        self.t_normal = torch.zeros(3, 0, device=dev)
+        self.loss_out = torch.zeros(1, dtype=torch.float64, device=dev)
+
+    def _rows(self, ts):
+        return [t[:self.n] for t in ts]
+
+    def add_keyframe(self, view, target_depth, target_normal) -> int:
+        """Register a keyframe with its target range (H, W) and normals (3, H, W), grow the map
+        from it by n_new slots and return the map size."""
+        if self.n + self.n_new > self.capacity:
+            raise ValueError("map capacity exhausted")
+        self.views.append(view)
+        self.ctx.set_views(self.views)
+        td = target_depth.reshape(-1).to(self.t_depth.device, torch.float32)
+        tn = target_normal.reshape(3, -1).to(self.t_depth.device, torch.float32)
+        self.t_depth = torch.cat([self.t_depth, td]).contiguous()
+        self.t_normal = torch.cat([self.t_normal, tn], 1).contiguous()
+        # only the new keyframe's pixels are drawn from
+        only_new = torch.zeros_like(self.t_depth)
+        o = self.ctx.offsets[-1]
+        only_new[o:o + td.numel()] = td
+        cfg = DensifyConfig(**{**self.densify_cfg.__dict__, "refine": self.n > 0})
+        depth = alpha = None
+        if self.n > 0:
+            depth, _, alpha = self.ctx.render(*self._rows(self.params))
+        self.ctx.densify(self.params, self.n, self.n_new, only_new, depth, alpha, cfg)
+        self.n += self.n_new
+        return self.n
+
+    def refine(self, iters: int) -> list[float]:
+        """Refinement iterations over the registered keyframes, each on the keyframes drawn for
+        it (a fresh random stream per call); returns each iteration's loss.  Sampling is off
+        outside this call, so renders cover every keyframe."""
+        m_pl, m_q, m_ls, v_pl, v_q, v_ls, step = self.state
+        self._refines = getattr(self, "_refines", 0) + 1
+        if self.draws > 0 and len(self.views) > 1:
+            self.ctx.set_view_sampling(self.draws, self.p_newest,
+                                       self.seed + 1000003 * self._refines)
+        losses = []
+        try:
+            for _ in range(int(iters)):
+                self.ctx.refine_step(self._rows(self.params),
+                                     (*self._rows((m_pl, m_q, m_ls, v_pl, v_q, v_ls)), step),
+                                     self.t_depth, self.t_normal, self.loss_cfg, self.adam_cfg,
+                                     self.loss_out)
+                losses.append(float(self.loss_out.item()))
+        finally:
+            self.ctx.set_view_sampling(0)
+        return losses
+
+    def render(self):
+        """Packed (depth, normal, alpha) of the registered keyframes for the current map."""
+        return self.ctx.render(*self._rows(self.params))
