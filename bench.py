@@ -243,8 +243,8 @@ def cpu_baseline(scene, views, targets, budget_s, seed=0):
 
     # grow the sample until it takes about the budget (a small run is dominated by fixed costs)
     k, t = 256, run(256)
-    while t < 0.5 * budget_s and k < (1 << 20):
-        k = int(min(1 << 20, max(2 * k, 0.9 * k * budget_s / max(t, 1e-6))))
+    while t < 0.5 * budget_s and k < (1 << 22):
+        k = int(min(1 << 22, max(2 * k, 0.9 * k * budget_s / max(t, 1e-6))))
         t = run(k)
     return {"value": k / t, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
             "sample": (f"FP64 oracle forward + loss + backward of {k} random pixels of keyframe "
