@@ -474,8 +474,12 @@ def run_reference(args):
                                v.elev_max, gD, gN, gO, culled=cul, pixels=px)
         return time.perf_counter() - t
 
-    tp = step(128)
-    k = int(max(32, 128 * per_step / max(tp, 1e-6)))
+    # size the per-step sample so that one step takes about per_step (a small sample is
+    # dominated by per-call fixed costs, so the size is grown geometrically)
+    k, t = 128, step(128)
+    while t < 0.5 * per_step and k < (1 << 22):
+        k = int(min(1 << 22, max(2 * k, 0.9 * k * per_step / max(t, 1e-6))))
+        t = step(k)
     for _ in range(W):
         step(k)
     total = sum(step(k) for _ in range(K))
@@ -485,7 +489,10 @@ def run_reference(args):
     return {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": K, "warmup": W, "ms_per_step": 1e3 * total / K, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": desc, "n_gaussians": scene.n, "keyframes": len(views)},
+            "config": {"workload": desc, "n_gaussians": scene.n, "keyframes": len(views),
+                       "pixels_per_step": sum(x.rows * x.cols for x in views),
+                       "step": "render + loss + backward + Adam over all keyframes",
+                       "parallelism": "replicas" if world > 1 else "single GPU"},
             "cpu_baseline": {"kind": "oracle", "cores": os.cpu_count(), "sample": sample,
                              "value": value, "unit": UNIT},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
