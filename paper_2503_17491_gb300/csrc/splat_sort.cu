@@ -63,29 +63,40 @@ __global__ void __launch_bounds__(kThreads) k_upsweep(const uint32_t *__restrict
     hist[static_cast<int64_t>(tid) * gridDim.x + blockIdx.x] = t;
 }
 
-// per digit (one warp each): exclusive scan of its per-CTA counts hist[d * grid + b] in place,
-// and the digit's total into dtot[d]
+// per digit (one warp each): exclusive scan of its kSortGrid per-CTA counts hist[d * grid + b]
+// in place, and the digit's total into dtot[d].  Each lane takes a run of kPer consecutive
+// counts, so all loads are issued before the one warp scan of the run sums.
 __global__ void __launch_bounds__(256) k_scan_digits(uint32_t *__restrict__ hist, int grid,
                                                      uint32_t *__restrict__ dtot)
 {
+    constexpr int kPer = (kSortGrid + 31) / 32;
     const int lane = threadIdx.x & 31;
     const int d = blockIdx.x * 8 + (threadIdx.x >> 5);
     if (d >= kRadix) return;
     uint32_t *h = hist + static_cast<int64_t>(d) * grid;
-    uint32_t carry = 0;
-    for (int b0 = 0; b0 < grid; b0 += 32) {
-        const int b = b0 + lane;
-        const uint32_t v = b < grid ? h[b] : 0u;
-        uint32_t x = v;
+    uint32_t v[kPer];
+    uint32_t sum = 0;
 #pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, x, o);
-            if (lane >= o) x += y;
-        }
-        if (b < grid) h[b] = carry + x - v;
-        carry += __shfl_sync(0xFFFFFFFFu, x, 31);
+    for (int i = 0; i < kPer; ++i) {
+        const int b = lane * kPer + i;
+        v[i] = b < grid ? h[b] : 0u;
+        sum += v[i];
     }
-    if (lane == 0) dtot[d] = carry;
+    uint32_t x = sum;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, x, o);
+        if (lane >= o) x += y;
+    }
+    uint32_t run = x - sum;
+#pragma unroll
+    for (int i = 0; i < kPer; ++i) {
+        const int b = lane * kPer + i;
+        if (b < grid) h[b] = run;
+        run += v[i];
+    }
+    const uint32_t total = __shfl_sync(0xFFFFFFFFu, x, 31);
+    if (lane == 0) dtot[d] = total;
 }
 
 __global__ void __launch_bounds__(kThreads) k_downsweep(
@@ -234,21 +245,33 @@ __global__ void __launch_bounds__(1024) k_scan_sums(uint32_t *__restrict__ block
                                                     int64_t max_pairs, uint32_t *d_count,
                                                     uint32_t *status)
 {
-    __shared__ unsigned long long s[1024];
-    const int tid = threadIdx.x;
+    __shared__ unsigned long long s_w[32];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const unsigned long long v = tid < grid ? block_sums[tid] : 0ull;
-    s[tid] = v;
-    __syncthreads();
-    for (int off = 1; off < 1024; off <<= 1) {
-        const unsigned long long a = tid >= off ? s[tid - off] : 0ull;
-        __syncthreads();
-        s[tid] += a;
-        __syncthreads();
+    unsigned long long x = v;   // warp inclusive scan, then the warps' totals scanned by warp 0
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const unsigned long long y = __shfl_up_sync(0xFFFFFFFFu, x, o);
+        if (lane >= o) x += y;
     }
-    const unsigned long long excl = s[tid] - v;
+    if (lane == 31) s_w[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+        const unsigned long long w = s_w[lane];
+        unsigned long long z = w;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned long long y = __shfl_up_sync(0xFFFFFFFFu, z, o);
+            if (lane >= o) z += y;
+        }
+        s_w[lane] = z - w;
+    }
+    __syncthreads();
+    const unsigned long long incl = x + s_w[warp];
+    const unsigned long long excl = incl - v;
     if (tid < grid) block_sums[tid] = excl > 0xFFFFFFFFull ? 0xFFFFFFFFu : static_cast<uint32_t>(excl);
     if (tid == 1023) {
-        const unsigned long long total = s[1023];
+        const unsigned long long total = incl;
         if (total > static_cast<unsigned long long>(max_pairs)) {
             atomicOr(status, SPLAT_STATUS_CAPACITY);
             *d_count = static_cast<uint32_t>(max_pairs);
