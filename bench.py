@@ -337,7 +337,7 @@ def run_ours(args):
     prof_params = [p.clone() for p in params0]
     pref = api.Refiner(prof_params, views, targets, mode="batched", cfg=cfg, max_pairs=max_pairs)
     pref.ctx.set_profiling(True)
-    fwd_ms, bwd_ms, fev, bev = [], [], [], []
+    fwd_ms, bwd_ms, fev, bev, stage_ms = [], [], [], [], []
     for i in range(max(3, min(args.steps, 10)) + 1):
         flush()
         pref.step()
@@ -349,6 +349,7 @@ def run_ours(args):
         bwd_ms.append(b)
         fev.append(s2["fwd_evals"])
         bev.append(s2["bwd_evals"])
+        stage_ms.append(pref.ctx.stage_times())
     kern = {"render_fwd": (statistics.mean(fwd_ms), statistics.mean(fev)),
             "render_bwd": (statistics.mean(bwd_ms), statistics.mean(bev))}
     dom = max(kern, key=lambda k: kern[k][0])
@@ -367,6 +368,28 @@ def run_ours(args):
                 "launch_ms": k_ms,
                 "other_kernel": {k: {"launch_ms": v[0], "evals": v[1]} for k, v in kern.items()
                                  if k != dom}}
+
+    # per-stage times of the same eager steps against the HBM roofline, with each stage's
+    # algorithmic bytes (what its definition reads and writes once): n primitives, V keyframes,
+    # nv (view, primitive) pairs that touch a tile, M list entries, T tiles, P pixels
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
+    n, V, nv, M, T = scene.n, len(views), s2["n_touching"], s2["n_pairs"], s2["n_tiles"]
+    passes = (max(int(T - 1).bit_length(), 1) + 7) // 8
+    stage_bytes = {"projection": 40 * n + 24 * n * V,
+                   "range sort": 12 * n * V + 68 * nv,
+                   "emission": 40 * nv + 8 * M,
+                   "tile sort": 20 * passes * M,
+                   "tile ranges": 29 * M + 20 * T,
+                   "loss": 52 * pixels,
+                   "fused Adam": 304 * n}
+    stages = {}
+    for name, nbytes in stage_bytes.items():
+        vals = [x[name] for x in stage_ms if x.get(name) is not None]
+        if not vals:
+            continue
+        ms = statistics.mean(vals)
+        stages[name] = {"ms": ms, "bytes": nbytes, "gbs": nbytes / (ms * 1e-3) / 1e9,
+                        "frac": nbytes / (ms * 1e-3) / 1e9 / hbm}
 
     # ---- plain: one launch sequence per keyframe, no graph ------------------------------------
     plain = None
@@ -427,6 +450,8 @@ def run_ours(args):
         "batched_over_plain": (plain["ms_per_step"] / ms_max) if plain else None,
         "gaussian_pixel_evals_per_s": world * evals_step / (ms_max * 1e-3),
         "roofline": roofline,
+        "stages": {"unit": "GB/s against the measured HBM copy bandwidth (algorithmic bytes; "
+                           "the compositing kernels are in roofline)", **stages},
         "cpu_baseline": cpu,
         "e2e": e2e,
         "gpu_launches": launches_per_step * args.steps,

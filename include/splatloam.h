@@ -164,6 +164,7 @@ typedef struct {
     int64_t n_pixels;         /* pixels of the registered views                      */
     int64_t n_tiles;          /* tiles of the registered views                       */
     int64_t kernel_launches;  /* kernels this context has launched since creation    */
+    int64_t n_touching;       /* (view, primitive) pairs that touch at least one tile */
 } splat_stats;
 
 /* ---- context ------------------------------------------------------------------------------ */
@@ -404,6 +405,12 @@ SPLAT_API int splat_get_stats(splat_ctx *ctx, splat_stats *out);
  * while the stream is being captured into a graph record nothing.  Errors: INVALID_ARG, CUDA. */
 SPLAT_API int splat_set_profiling(splat_ctx *ctx, int enable);
 SPLAT_API int splat_kernel_times(splat_ctx *ctx, float *fwd_ms, float *bwd_ms);
+/* With profiling enabled: the durations (ms, waiting for the events) of the stages of the last
+ * profiled render and refinement step, ms[7] = projection, range sort, emission (count, scan,
+ * emit), tile sort, tile ranges and work order, loss, fused Adam; -1 for a stage not recorded
+ * since profiling was enabled (the last two come from splat_refine_step only).
+ * Errors: INVALID_ARG, CUDA. */
+SPLAT_API int splat_stage_times(splat_ctx *ctx, float *ms);
 
 /* Copy workspace state of the last render to host memory (synchronising), for tests and
  * profiling.  which = 0: sorted global tile ids (uint32, n_pairs); 1: pair ids of the sorted

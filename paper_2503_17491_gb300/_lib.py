@@ -60,7 +60,8 @@ class splat_adam_config(ctypes.Structure):
 
 class splat_stats(ctypes.Structure):
     _fields_ = [("n_pairs", _I64), ("fwd_evals", _I64), ("bwd_evals", _I64),
-                ("n_pixels", _I64), ("n_tiles", _I64), ("kernel_launches", _I64)]
+                ("n_pixels", _I64), ("n_tiles", _I64), ("kernel_launches", _I64),
+                ("n_touching", _I64)]
 
 
 SPLAT_OK = 0
@@ -104,6 +105,7 @@ SIGNATURES = {
     "splat_get_status": ([_P, ctypes.POINTER(ctypes.c_uint32)], _I),
     "splat_get_stats": ([_P, ctypes.POINTER(splat_stats)], _I),
     "splat_debug_copy": ([_P, _I32, _P, _I64], _I64),
+    "splat_stage_times": ([_P, _P], _I),
     "splat_set_profiling": ([_P, _I], _I),
     "splat_render_noalloc": ([ctypes.POINTER(splat_gaussians), _P,
                               ctypes.POINTER(splat_lidar_intrinsics),

@@ -320,7 +320,18 @@ class SplatContext:
         s = _lib.splat_stats()
         _lib.check(self.lib.splat_get_stats(self.h, ctypes.byref(s)), "splat_get_stats")
         return dict(n_pairs=s.n_pairs, fwd_evals=s.fwd_evals, bwd_evals=s.bwd_evals,
-                    n_pixels=s.n_pixels, n_tiles=s.n_tiles, kernel_launches=s.kernel_launches)
+                    n_pixels=s.n_pixels, n_tiles=s.n_tiles, kernel_launches=s.kernel_launches,
+                    n_touching=s.n_touching)
+
+    STAGES = ("projection", "range sort", "emission", "tile sort", "tile ranges", "loss",
+              "fused Adam")
+
+    def stage_times(self) -> dict:
+        """Durations (ms) of the stages of the last profiled render / refinement step
+        (splat_stage_times); None for a stage not recorded."""
+        ms = (ctypes.c_float * 7)()
+        _lib.check(self.lib.splat_stage_times(self.h, ms), "splat_stage_times")
+        return {k: (float(v) if v >= 0 else None) for k, v in zip(self.STAGES, ms)}
 
     def set_profiling(self, on: bool):
         _lib.check(self.lib.splat_set_profiling(self.h, 1 if on else 0), "splat_set_profiling")

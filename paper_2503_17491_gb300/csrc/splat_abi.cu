@@ -105,8 +105,14 @@ struct splat_ctx {
     unsigned long long *d_grow_sums = nullptr;  // map growth: block sums, Q, offset
     unsigned long long *d_evals = nullptr;      // [0] forward, [1] backward
 
-    // profiling events around the compositing kernels: [0,1] forward, [2,3] backward
+    // profiling events: [0,1] forward compositing, [2,3] backward compositing, then one event
+    // after each stage of the last profiled render / refinement step (stage_ev[k] ends stage k,
+    // stage_ev[0] is recorded before the projection): projection, range sort, emission, tile
+    // sort, ranges and work order, loss, fused Adam
     cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+    static constexpr int kStageEvents = 8;
+    cudaEvent_t stage_ev[kStageEvents] = {};
+    bool stage_rec[kStageEvents] = {};
     bool profiling = false;
     bool rec_fwd = false, rec_bwd = false;
     int64_t launches = 0;
@@ -198,6 +204,15 @@ int render_core(splat_ctx *ctx, const splat_gaussians *g, float *depth, float *n
                                       ctx->d_active, st));
         active = ctx->d_active;
     }
+    const bool prof = ctx->profiling && !capturing(st);
+    auto stage_mark = [&](int k) -> cudaError_t {
+        if (!prof) return cudaSuccess;
+        ctx->stage_rec[k] = true;
+        return cudaEventRecord(ctx->stage_ev[k], st);
+    };
+    if (prof)
+        for (int k = 0; k < splat_ctx::kStageEvents; ++k) ctx->stage_rec[k] = false;
+    CK(stage_mark(0));
     CK(splat::launch_project(reinterpret_cast<const float4 *>(g->pos_logit),
                              reinterpret_cast<const float4 *>(g->quat_wxyz),
                              reinterpret_cast<const float2 *>(g->log_scale), n, ctx->d_views,
@@ -205,17 +220,21 @@ int render_core(splat_ctx *ctx, const splat_gaussians *g, float *depth, float *n
                              ctx->cfg.flip_normals,
                              ctx->d_recs, ctx->d_dkeys, ctx->d_dvals, cnt + 1, cnt + 4, st,
                              active));
+    CK(stage_mark(1));
     uint32_t *dk, *dv;
     // the range sort drops the pairs that touch no tile (key 0xFFFFFFFF) in its first pass
     CK(splat::radix_sort_pairs(ctx->d_dkeys, ctx->d_dvals, ctx->d_dkeys2, ctx->d_dvals2, nullptr,
                                npv, 32, ctx->d_hist, &dk, &dv, st, cnt + 4));
+    CK(stage_mark(2));
     CK(splat::launch_emit(dv, npv, cnt + 4, ctx->d_recs, ctx->d_views, n, th, tw,
                           ctx->d_block_sums, ctx->d_tkeys, ctx->d_tvals, ctx->cap.max_pairs, cnt,
                           cnt + 1, st));
+    CK(stage_mark(3));
     uint32_t *tk, *tv;
     CK(splat::radix_sort_pairs(ctx->d_tkeys, ctx->d_tvals, ctx->d_tkeys2, ctx->d_tvals2, cnt,
                                ctx->cap.max_pairs, bits_for(ctx->n_tiles), ctx->d_hist, &tk, &tv,
                                st));
+    CK(stage_mark(4));
     // the tile sort's other buffers are free: they take the entries' tile rectangles and the
     // blocks each meets
     uint32_t *rects = tv == ctx->d_tvals ? ctx->d_tvals2 : ctx->d_tvals;
@@ -223,6 +242,7 @@ int render_core(splat_ctx *ctx, const splat_gaussians *g, float *depth, float *n
     CK(splat::launch_ranges(tk, tv, ctx->d_recs, ctx->d_tileinfo, th, tw, cnt,
                             ctx->cap.max_pairs, ctx->d_ranges, ctx->n_tiles, rects, blocks, st));
     CK(splat::launch_order_tiles(ctx->d_ranges, ctx->n_tiles, ctx->d_tile_order, st));
+    CK(stage_mark(5));
     ctx->sorted_keys = tk;
     ctx->sorted_vals = tv;
     ctx->entry_rect = rects;
@@ -233,7 +253,6 @@ int render_core(splat_ctx *ctx, const splat_gaussians *g, float *depth, float *n
     a.alpha = alpha;
     a.queue = cnt + 2;
     a.evals = ctx->d_evals;
-    const bool prof = ctx->profiling && !capturing(st);
     if (prof) CK(cudaEventRecord(ctx->ev[0], st));
     CK(splat::launch_render_fwd(a, th, tw, ctx->grid_fwd, st));
     if (prof) {
@@ -290,6 +309,8 @@ void free_ctx(splat_ctx *c)
     for (void *p : ptrs)
         if (p) cudaFree(p);
     for (cudaEvent_t e : c->ev)
+        if (e) cudaEventDestroy(e);
+    for (cudaEvent_t e : c->stage_ev)
         if (e) cudaEventDestroy(e);
     delete c;
 }
@@ -397,6 +418,8 @@ SPLAT_API int splat_ctx_create(const splat_render_config *cfg, const splat_capac
     if (e == cudaSuccess) e = dalloc(&c->d_counters, 8);
     if (e == cudaSuccess) e = dalloc(&c->d_evals, 2);
     for (int k = 0; k < 4 && e == cudaSuccess; ++k) e = cudaEventCreate(&c->ev[k]);
+    for (int k = 0; k < splat_ctx::kStageEvents && e == cudaSuccess; ++k)
+        e = cudaEventCreate(&c->stage_ev[k]);
     if (e == cudaSuccess) e = cudaMemset(c->d_counters, 0, 8 * sizeof(uint32_t));
     if (e == cudaSuccess) e = cudaMemset(c->d_evals, 0, 2 * sizeof(unsigned long long));
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
@@ -831,6 +854,11 @@ SPLAT_API int splat_refine_step(splat_ctx *ctx, float *pos_logit, float *quat, f
                           ctx->d_views, ctx->n_views,
                           ctx->samp_draws > 0 ? ctx->d_active : nullptr,
                           loss_cfg->normal_mode));
+    const bool prof = ctx->profiling && !capturing(st);
+    if (prof) {
+        CK(cudaEventRecord(ctx->stage_ev[6], st));
+        ctx->stage_rec[6] = true;
+    }
     r = backward_core(ctx, &g, gd, gn, ga, st);
     if (r) return r;
     splat::AdamArgs a{};
@@ -856,6 +884,10 @@ SPLAT_API int splat_refine_step(splat_ctx *ctx, float *pos_logit, float *quat, f
     a.tau_s = loss_cfg->tau_s;
     a.loss_out = loss_out;
     CK(splat::launch_adam_fused(a, ctx->d_wgrad, st));
+    if (prof) {
+        CK(cudaEventRecord(ctx->stage_ev[7], st));
+        ctx->stage_rec[7] = true;
+    }
     CK(splat::launch_step_inc(step, st));
     ctx->launches += 3;   // loss, fused Adam, step counter
     return SPLAT_OK;
@@ -940,11 +972,12 @@ SPLAT_API int splat_get_stats(splat_ctx *ctx, splat_stats *out)
 {
     if (!ctx || !out) return SPLAT_ERR_INVALID_ARG;
     CK(cudaDeviceSynchronize());
-    uint32_t m = 0;
+    uint32_t c[5] = {0, 0, 0, 0, 0};
     unsigned long long ev[2] = {0, 0};
-    CK(cudaMemcpy(&m, ctx->d_counters, sizeof m, cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(c, ctx->d_counters, sizeof c, cudaMemcpyDeviceToHost));
     CK(cudaMemcpy(ev, ctx->d_evals, sizeof ev, cudaMemcpyDeviceToHost));
-    out->n_pairs = m;
+    out->n_pairs = c[0];
+    out->n_touching = c[4];
     out->fwd_evals = static_cast<int64_t>(ev[0]);
     out->bwd_evals = static_cast<int64_t>(ev[1]);
     out->n_pixels = ctx->n_pixels;
@@ -958,6 +991,7 @@ SPLAT_API int splat_set_profiling(splat_ctx *ctx, int enable)
     if (!ctx) return SPLAT_ERR_INVALID_ARG;
     ctx->profiling = enable != 0;
     ctx->rec_fwd = ctx->rec_bwd = false;
+    for (bool &b : ctx->stage_rec) b = false;
     return SPLAT_OK;
 }
 
@@ -973,6 +1007,33 @@ SPLAT_API int splat_kernel_times(splat_ctx *ctx, float *fwd_ms, float *bwd_ms)
     if (ctx->rec_bwd) {
         CK(cudaEventSynchronize(ctx->ev[3]));
         CK(cudaEventElapsedTime(bwd_ms, ctx->ev[2], ctx->ev[3]));
+    }
+    return SPLAT_OK;
+}
+
+SPLAT_API int splat_stage_times(splat_ctx *ctx, float *ms)
+{
+    if (!ctx || !ms) return SPLAT_ERR_INVALID_ARG;
+    // stage k of the render runs between stage events k and k + 1; the loss between the end of
+    // the forward compositing and event 6, the fused Adam between the end of the backward and 7
+    struct Span {
+        cudaEvent_t a, b;
+        bool ok;
+    };
+    const Span spans[7] = {
+        {ctx->stage_ev[0], ctx->stage_ev[1], ctx->stage_rec[0] && ctx->stage_rec[1]},
+        {ctx->stage_ev[1], ctx->stage_ev[2], ctx->stage_rec[1] && ctx->stage_rec[2]},
+        {ctx->stage_ev[2], ctx->stage_ev[3], ctx->stage_rec[2] && ctx->stage_rec[3]},
+        {ctx->stage_ev[3], ctx->stage_ev[4], ctx->stage_rec[3] && ctx->stage_rec[4]},
+        {ctx->stage_ev[4], ctx->stage_ev[5], ctx->stage_rec[4] && ctx->stage_rec[5]},
+        {ctx->ev[1], ctx->stage_ev[6], ctx->rec_fwd && ctx->stage_rec[6]},
+        {ctx->ev[3], ctx->stage_ev[7], ctx->rec_bwd && ctx->stage_rec[7]},
+    };
+    for (int k = 0; k < 7; ++k) {
+        ms[k] = -1.0f;
+        if (!spans[k].ok) continue;
+        CK(cudaEventSynchronize(spans[k].b));
+        CK(cudaEventElapsedTime(&ms[k], spans[k].a, spans[k].b));
     }
     return SPLAT_OK;
 }
