@@ -240,14 +240,24 @@ __global__ void __launch_bounds__(kThreads) k_count_sums(const uint32_t *__restr
     }
 }
 
-// exclusive scan of the CTA sums (grid <= 1024 entries); total -> *d_count (saturated)
+// exclusive scan of the CTA sums (grid <= kScanGrid entries, kScanPer consecutive ones per
+// thread); total -> *d_count (saturated)
+constexpr int kScanPer = kScanGrid / 1024;
+static_assert(kScanGrid % 1024 == 0, "the CTA-sum scan takes whole runs of 1024");
 __global__ void __launch_bounds__(1024) k_scan_sums(uint32_t *__restrict__ block_sums, int grid,
                                                     int64_t max_pairs, uint32_t *d_count,
                                                     uint32_t *status)
 {
     __shared__ unsigned long long s_w[32];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const unsigned long long v = tid < grid ? block_sums[tid] : 0ull;
+    uint32_t e[kScanPer];
+    unsigned long long v = 0;
+#pragma unroll
+    for (int i = 0; i < kScanPer; ++i) {
+        const int b = tid * kScanPer + i;
+        e[i] = b < grid ? block_sums[b] : 0u;
+        v += e[i];
+    }
     unsigned long long x = v;   // warp inclusive scan, then the warps' totals scanned by warp 0
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
@@ -268,8 +278,13 @@ __global__ void __launch_bounds__(1024) k_scan_sums(uint32_t *__restrict__ block
     }
     __syncthreads();
     const unsigned long long incl = x + s_w[warp];
-    const unsigned long long excl = incl - v;
-    if (tid < grid) block_sums[tid] = excl > 0xFFFFFFFFull ? 0xFFFFFFFFu : static_cast<uint32_t>(excl);
+    unsigned long long run = incl - v;
+#pragma unroll
+    for (int i = 0; i < kScanPer; ++i) {
+        const int b = tid * kScanPer + i;
+        if (b < grid) block_sums[b] = run > 0xFFFFFFFFull ? 0xFFFFFFFFu : static_cast<uint32_t>(run);
+        run += e[i];
+    }
     if (tid == 1023) {
         const unsigned long long total = incl;
         if (total > static_cast<unsigned long long>(max_pairs)) {
@@ -463,7 +478,7 @@ cudaError_t launch_ranges(const uint32_t *tile_keys, const uint32_t *tile_vals,
 {
     cudaError_t e = cudaMemsetAsync(ranges, 0, sizeof(uint2) * static_cast<size_t>(n_tiles), st);
     if (e != cudaSuccess) return e;
-    k_ranges<<<4 * kSortGrid, 256, 0, st>>>(tile_keys, tile_vals, recs, tiles, tile_h, tile_w,
+    k_ranges<<<kRangesGrid, 256, 0, st>>>(tile_keys, tile_vals, recs, tiles, tile_h, tile_w,
                                             d_count, max_pairs, ranges, entry_rect,
                                             entry_blocks);
     return cudaGetLastError();
