@@ -86,6 +86,7 @@ struct splat_ctx {
     // workspace
     PairRec *d_recs = nullptr;
     uint32_t *d_dkeys = nullptr, *d_dvals = nullptr, *d_dkeys2 = nullptr, *d_dvals2 = nullptr;
+    uint64_t *d_trect = nullptr, *d_srect = nullptr;   // pair tile rectangles, and in range order
     uint32_t *d_tkeys = nullptr, *d_tvals = nullptr, *d_tkeys2 = nullptr, *d_tvals2 = nullptr;
     uint32_t *d_block_sums = nullptr, *d_hist = nullptr;
     uint2 *d_ranges = nullptr;
@@ -218,17 +219,19 @@ int render_core(splat_ctx *ctx, const splat_gaussians *g, float *depth, float *n
                              reinterpret_cast<const float2 *>(g->log_scale), n, ctx->d_views,
                              ctx->n_views, ctx->cfg.sigma_cut, ctx->cfg.alpha_min, th, tw,
                              ctx->cfg.flip_normals,
-                             ctx->d_recs, ctx->d_dkeys, ctx->d_dvals, cnt + 1, cnt + 4, st,
+                             ctx->d_recs, ctx->d_dkeys, ctx->d_dvals, ctx->d_trect, cnt + 1,
+                             cnt + 4, st,
                              active));
     CK(stage_mark(1));
     uint32_t *dk, *dv;
     // the range sort drops the pairs that touch no tile (key 0xFFFFFFFF) in its first pass
+    // (its last pass also lays the pairs' tile rectangles out in range order for the emission)
     CK(splat::radix_sort_pairs(ctx->d_dkeys, ctx->d_dvals, ctx->d_dkeys2, ctx->d_dvals2, nullptr,
-                               npv, 32, ctx->d_hist, &dk, &dv, st, cnt + 4));
+                               npv, 32, ctx->d_hist, &dk, &dv, st, cnt + 4, ctx->d_trect,
+                               ctx->d_srect));
     CK(stage_mark(2));
-    CK(splat::launch_emit(dv, npv, cnt + 4, ctx->d_recs, ctx->d_views, n, th, tw,
-                          ctx->d_block_sums, ctx->d_tkeys, ctx->d_tvals, ctx->cap.max_pairs, cnt,
-                          cnt + 1, st));
+    CK(splat::launch_emit(dv, ctx->d_srect, npv, cnt + 4, ctx->d_views, n, ctx->d_block_sums,
+                          ctx->d_tkeys, ctx->d_tvals, ctx->cap.max_pairs, cnt, cnt + 1, st));
     CK(stage_mark(3));
     uint32_t *tk, *tv;
     CK(splat::radix_sort_pairs(ctx->d_tkeys, ctx->d_tvals, ctx->d_tkeys2, ctx->d_tvals2, cnt,
@@ -300,7 +303,7 @@ int backward_core(splat_ctx *ctx, const splat_gaussians *g, const float *gD, con
 void free_ctx(splat_ctx *c)
 {
     void *ptrs[] = {c->d_views, c->d_frames, c->d_tile_view, c->d_recs, c->d_dkeys, c->d_dvals,
-                    c->d_dkeys2, c->d_dvals2, c->d_tkeys, c->d_tvals, c->d_tkeys2, c->d_tvals2,
+                    c->d_dkeys2, c->d_dvals2, c->d_trect, c->d_srect, c->d_tkeys, c->d_tvals, c->d_tkeys2, c->d_tvals2,
                     c->d_block_sums, c->d_hist, c->d_ranges, c->d_tfinal, c->d_nlast, c->d_wgrad,
                     c->d_pose, c->d_rec, c->d_rec_prev, c->d_rec_head, c->d_rec_fill,
                     c->d_samp_thr, c->d_active, c->d_grow_sums,
@@ -390,6 +393,8 @@ SPLAT_API int splat_ctx_create(const splat_render_config *cfg, const splat_capac
     if (e == cudaSuccess) e = dalloc(&c->d_dvals, mpv);
     if (e == cudaSuccess) e = dalloc(&c->d_dkeys2, mpv);
     if (e == cudaSuccess) e = dalloc(&c->d_dvals2, mpv);
+    if (e == cudaSuccess) e = dalloc(&c->d_trect, mpv);
+    if (e == cudaSuccess) e = dalloc(&c->d_srect, mpv);
     if (e == cudaSuccess) e = dalloc(&c->d_tkeys, M);
     if (e == cudaSuccess) e = dalloc(&c->d_tvals, M);
     if (e == cudaSuccess) e = dalloc(&c->d_tkeys2, M);

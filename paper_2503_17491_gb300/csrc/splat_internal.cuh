@@ -184,6 +184,17 @@ __host__ __device__ inline void tile_cols_of(int c0, int nc, int cols, int tw, i
     *ntc = n;
 }
 
+// A pair's tile rectangle in one word: first tile row, tile rows, first tile column, tile columns
+// (cyclic modulo the view's tile columns), 16 bits each; every field is below 2^13 for images
+// of at most 32,767 rows and columns and tiles of at least 4 pixels a side.
+__host__ __device__ inline uint64_t pack_tile_rect(int tr0, int ntr, int tc0, int ntc)
+{
+    return static_cast<uint64_t>(static_cast<uint16_t>(tr0)) |
+           static_cast<uint64_t>(static_cast<uint16_t>(ntr)) << 16 |
+           static_cast<uint64_t>(static_cast<uint16_t>(tc0)) << 32 |
+           static_cast<uint64_t>(static_cast<uint16_t>(ntc)) << 48;
+}
+
 // ---------------------------------------------------------------------------------------------
 // float-pair ("double-float") arithmetic, used where the sensor-frame centre of a primitive
 // must keep more than 24 bits (the lateral offset of a far splat from a ray).
@@ -298,11 +309,13 @@ __device__ __forceinline__ void chain_params(const float4 pl, const float4 q, co
 // ---------------------------------------------------------------------------------------------
 struct Workspace;   // host-side bookkeeping, defined in splat_abi.cu
 
+// trect[p]: the pair's tile rectangle as one word (see pack_tile_rect), 0 when it touches none
 cudaError_t launch_project(const float4 *pos_logit, const float4 *quat, const float2 *log_scale,
                            int64_t n, const ViewDesc *views, int n_views, float sigma,
                            float alpha_min, int tile_h, int tile_w, int flip_normals,
-                           PairRec *recs, uint32_t *dkeys, uint32_t *dvals, uint32_t *status,
-                           uint32_t *n_valid, cudaStream_t st, const uint8_t *active = nullptr);
+                           PairRec *recs, uint32_t *dkeys, uint32_t *dvals, uint64_t *trect,
+                           uint32_t *status, uint32_t *n_valid, cudaStream_t st,
+                           const uint8_t *active = nullptr);
 
 // stable LSD radix sort of (uint32 key, uint32 value) pairs on key bits [0, bits);
 // the count is read on the device from *d_count (clamped to max_n); result lands in
@@ -313,10 +326,13 @@ constexpr int kHistWords = kSortGrid * 256 + 256;   // per-CTA digit counts + di
 // With d_count_kept non-null the first pass also drops every item whose key is 0xFFFFFFFF (which
 // would sort last) and the later passes sort the d_count_kept items left, which the caller has
 // counted beforehand.
+// With aux_out non-null the last pass also writes aux_out[i] = aux_in[value of sorted item i]:
+// a copy of per-value data in sorted order, so that the stages after the sort read it in order.
 cudaError_t radix_sort_pairs(uint32_t *keys, uint32_t *vals, uint32_t *keys_alt, uint32_t *vals_alt,
                              const uint32_t *d_count, int64_t max_n, int bits, uint32_t *tmp_hist,
                              uint32_t **keys_out, uint32_t **vals_out, cudaStream_t st,
-                             const uint32_t *d_count_kept = nullptr);
+                             const uint32_t *d_count_kept = nullptr,
+                             const uint64_t *aux_in = nullptr, uint64_t *aux_out = nullptr);
 
 // offsets of every sorted pair, emission of (global tile, pair id) entries, total pair count
 // emission grid: CTAs over the sorted pairs (measured on GB300: 1024 -> 4096 CTAs took the
@@ -327,11 +343,12 @@ constexpr int kScanGrid = 4096;
 // (0.089 ms on 6.1 M entries, against 0.113 ms with 16 per SM)
 constexpr int kRangesGrid = 912;
 // n_valid: device count of the leading sorted pairs that touch a tile (the rest touch none)
-cudaError_t launch_emit(const uint32_t *sorted_pair_ids, int64_t n_pairs_total,
-                        const uint32_t *n_valid, const PairRec *recs, const ViewDesc *views,
-                        int64_t n_per_view, int tile_h, int tile_w, uint32_t *block_sums,
-                        uint32_t *tile_keys, uint32_t *tile_vals, int64_t max_pairs,
-                        uint32_t *d_count, uint32_t *status, cudaStream_t st);
+// sorted_trect[j]: the tile rectangle of sorted pair j (the range sort's copy of trect)
+cudaError_t launch_emit(const uint32_t *sorted_pair_ids, const uint64_t *sorted_trect,
+                        int64_t n_pairs_total, const uint32_t *n_valid, const ViewDesc *views,
+                        int64_t n_per_view, uint32_t *block_sums, uint32_t *tile_keys,
+                        uint32_t *tile_vals, int64_t max_pairs, uint32_t *d_count,
+                        uint32_t *status, cudaStream_t st);
 
 // Pixel rectangle of a (view, primitive) record inside tile (tr, tc) of a tile_h x tile_w
 // tiling, packed as 4 bytes (r_lo, r_hi, c_lo, c_hi) with the record's normal-flip bit in bit 31;

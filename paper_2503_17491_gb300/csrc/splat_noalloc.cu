@@ -44,7 +44,9 @@ constexpr size_t kOffDkeys = align256(kOffRecs + sizeof(PairRec) * kMaxGaussians
 constexpr size_t kOffDvals = align256(kOffDkeys + 4 * kMaxGaussians);
 constexpr size_t kOffDkeys2 = align256(kOffDvals + 4 * kMaxGaussians);
 constexpr size_t kOffDvals2 = align256(kOffDkeys2 + 4 * kMaxGaussians);
-constexpr size_t kOffTkeys = align256(kOffDvals2 + 4 * kMaxGaussians);
+constexpr size_t kOffTrect = align256(kOffDvals2 + 4 * kMaxGaussians);
+constexpr size_t kOffSrect = align256(kOffTrect + 8 * kMaxGaussians);
+constexpr size_t kOffTkeys = align256(kOffSrect + 8 * kMaxGaussians);
 constexpr size_t kOffTvals = align256(kOffTkeys + 4 * kMaxPairs);
 constexpr size_t kOffTkeys2 = align256(kOffTvals + 4 * kMaxPairs);
 constexpr size_t kOffTvals2 = align256(kOffTkeys2 + 4 * kMaxPairs);
@@ -242,6 +244,8 @@ extern "C" SPLAT_API int splat_render_noalloc(const splat_gaussians *g,
     uint32_t *dvals = reinterpret_cast<uint32_t *>(base + kOffDvals);
     uint32_t *dkeys2 = reinterpret_cast<uint32_t *>(base + kOffDkeys2);
     uint32_t *dvals2 = reinterpret_cast<uint32_t *>(base + kOffDvals2);
+    uint64_t *trect = reinterpret_cast<uint64_t *>(base + kOffTrect);
+    uint64_t *srect = reinterpret_cast<uint64_t *>(base + kOffSrect);
     uint32_t *tkeys = reinterpret_cast<uint32_t *>(base + kOffTkeys);
     uint32_t *tvals = reinterpret_cast<uint32_t *>(base + kOffTvals);
     uint32_t *tkeys2 = reinterpret_cast<uint32_t *>(base + kOffTkeys2);
@@ -271,13 +275,12 @@ extern "C" SPLAT_API int splat_render_noalloc(const splat_gaussians *g,
                                 reinterpret_cast<const float4 *>(g->quat_wxyz),
                                 reinterpret_cast<const float2 *>(g->log_scale), n, view, 1,
                                 cfg.sigma_cut, cfg.alpha_min, th, tw, cfg.flip_normals, recs, dkeys,
-                                dvals,
-                                cnt + 1, cnt + 4, st));
+                                dvals, trect, cnt + 1, cnt + 4, st));
     uint32_t *dk, *dv;
-    NA_CK(splat::radix_sort_pairs(dkeys, dvals, dkeys2, dvals2, nullptr, n, 32, hist, &dk, &dv, st));
-    NA_CK(splat::launch_emit(dv, n, cnt + 4, recs, view, n, th, tw, block_sums, tkeys, tvals,
-                             kMaxPairs, cnt,
-                             cnt + 1, st));
+    NA_CK(splat::radix_sort_pairs(dkeys, dvals, dkeys2, dvals2, nullptr, n, 32, hist, &dk, &dv, st,
+                                  nullptr, trect, srect));
+    NA_CK(splat::launch_emit(dv, srect, n, cnt + 4, view, n, block_sums, tkeys, tvals, kMaxPairs,
+                             cnt, cnt + 1, st));
     uint32_t *tk, *tv;
     NA_CK(splat::radix_sort_pairs(tkeys, tvals, tkeys2, tvals2, cnt, kMaxPairs, bits_for(n_tiles),
                                   hist, &tk, &tv, st));

@@ -11,8 +11,10 @@
 // contract_atan2, contract_exp, contract_log), never through a math library.
 //
 // One thread per primitive reads its 40 bytes once (coalesced float4/float2 loads) and loops
-// over the views; each (view, primitive) record is 16 bytes.  The range-sort keys and pair ids
-// are written here too, so the sort starts from this kernel's output.
+// over the views; each (view, primitive) record is 16 bytes, plus one 8-byte word with the
+// pair's tile rectangle that the range sort lays out in range order for the emission.  The
+// range-sort keys and pair ids are written here too, so the sort starts from this kernel's
+// output.
 
 #include <cmath>
 
@@ -138,7 +140,8 @@ __device__ __forceinline__ void elev_candidate(float z, float r, float &zh, floa
 // (where z / |xy| is stationary along the edge), and the pole the z axis reaches.  Returns the tile count and
 // fills the record's pixel rectangle.
 __device__ uint32_t contract_bbox(v3 ba, v3 bb, v3 bc, float o, float alpha_min, float sigma,
-                                  const ViewDesc &vd, int tile_h, int tile_w, PairRec &rec)
+                                  const ViewDesc &vd, int tile_h, int tile_w, PairRec &rec,
+                                  uint64_t &trect)
 {
     float x = o / alpha_min;
     if (x < 0.999f) return 0u;
@@ -258,15 +261,17 @@ __device__ uint32_t contract_bbox(v3 ba, v3 bb, v3 bc, float o, float alpha_min,
     rec.r1 = static_cast<int16_t>(r1);
     rec.c0 = static_cast<int16_t>(c0);
     rec.nc = static_cast<int16_t>(nc);
-    return static_cast<uint32_t>((r1 / tile_h - r0 / tile_h + 1) * ntc);
+    const int ntr = r1 / tile_h - r0 / tile_h + 1;
+    trect = pack_tile_rect(r0 / tile_h, ntr, tc0, ntc);
+    return static_cast<uint32_t>(ntr * ntc);
 }
 
 __global__ void __launch_bounds__(256) k_project(
     const float4 *__restrict__ pos_logit, const float4 *__restrict__ quat,
     const float2 *__restrict__ log_scale, int64_t n, const ViewDesc *__restrict__ views,
     int n_views, float sigma, float alpha_min, int tile_h, int tile_w, int flip_normals,
-    PairRec *__restrict__ recs,
-    uint32_t *__restrict__ dkeys, uint32_t *__restrict__ dvals, uint32_t *__restrict__ status,
+    PairRec *__restrict__ recs, uint32_t *__restrict__ dkeys, uint32_t *__restrict__ dvals,
+    uint64_t *__restrict__ trect, uint32_t *__restrict__ status,
     uint32_t *__restrict__ n_valid, const uint8_t *__restrict__ active)
 {
     const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
@@ -310,6 +315,7 @@ __global__ void __launch_bounds__(256) k_project(
         rec.r0 = rec.r1 = rec.c0 = rec.nc = 0;
         rec.kappa = 0.0f;
         rec.cf = ok ? 0u : kPairInvalid;
+        uint64_t tr = 0;
         if (ok) {
             // C3: sensor frame with the binary32 T^c_w
             const v3 ra = rot(vd.R_hi, ta), rb = rot(vd.R_hi, tb), rm = rot(vd.R_hi, mu);
@@ -332,9 +338,11 @@ __global__ void __launch_bounds__(256) k_project(
             const bool below = vd.cull_t_bot * rxy - bc.z > reach * vd.cull_l_bot;
             // C4: bounding box (views not sampled for this step take no pairs)
             if (!(clear && (above || below)) && !(active && !active[v]))
-                rec.cf |= contract_bbox(ba, bb, bc, oc, alpha_min, sigma, vd, tile_h, tile_w, rec);
+                rec.cf |= contract_bbox(ba, bb, bc, oc, alpha_min, sigma, vd, tile_h, tile_w, rec,
+                                        tr);
         }
         recs[p] = rec;
+        trect[p] = (rec.cf & kCountMask) ? tr : 0ull;
         dkeys[p] = (rec.cf & kCountMask) ? __float_as_uint(rec.kappa) : 0xFFFFFFFFu;
         dvals[p] = static_cast<uint32_t>(p);
         nv += (rec.cf & kCountMask) ? 1u : 0u;
@@ -351,14 +359,15 @@ __global__ void __launch_bounds__(256) k_project(
 cudaError_t launch_project(const float4 *pos_logit, const float4 *quat, const float2 *log_scale,
                            int64_t n, const ViewDesc *views, int n_views, float sigma,
                            float alpha_min, int tile_h, int tile_w, int flip_normals,
-                           PairRec *recs, uint32_t *dkeys, uint32_t *dvals, uint32_t *status,
-                           uint32_t *n_valid, cudaStream_t st, const uint8_t *active)
+                           PairRec *recs, uint32_t *dkeys, uint32_t *dvals, uint64_t *trect,
+                           uint32_t *status, uint32_t *n_valid, cudaStream_t st,
+                           const uint8_t *active)
 {
     if (n <= 0) return cudaSuccess;
     const unsigned grid = static_cast<unsigned>((n + 255) / 256);
     k_project<<<grid, 256, 0, st>>>(pos_logit, quat, log_scale, n, views, n_views, sigma,
                                     alpha_min, tile_h, tile_w, flip_normals, recs, dkeys, dvals,
-                                    status, n_valid, active);
+                                    trect, status, n_valid, active);
     return cudaGetLastError();
 }
 

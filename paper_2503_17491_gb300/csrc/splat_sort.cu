@@ -103,7 +103,8 @@ __global__ void __launch_bounds__(kThreads) k_downsweep(
     const uint32_t *__restrict__ keys_in, const uint32_t *__restrict__ vals_in,
     uint32_t *__restrict__ keys_out, uint32_t *__restrict__ vals_out, const uint32_t *d_count,
     int64_t max_n, int shift, int drop_max, const uint32_t *__restrict__ hist,
-    const uint32_t *__restrict__ dtot)
+    const uint32_t *__restrict__ dtot, const uint64_t *__restrict__ aux_in,
+    uint64_t *__restrict__ aux_out)
 {
     __shared__ uint32_t s_base[kRadix];          // running global offset per digit
     __shared__ uint32_t s_wcnt[kWarps][kRadix];  // per-warp digit counts -> warp prefixes
@@ -200,6 +201,7 @@ __global__ void __launch_bounds__(kThreads) k_downsweep(
             const uint32_t pos = s_base[d] + (static_cast<uint32_t>(i) - s_toff[d]);
             keys_out[pos] = k;
             vals_out[pos] = s_val[i];
+            if (aux_out) aux_out[pos] = aux_in[s_val[i]];
         }
         __syncthreads();
         s_base[tid] += s_tile[tid];
@@ -211,15 +213,14 @@ __global__ void __launch_bounds__(kThreads) k_downsweep(
 // emission (K2)
 // ---------------------------------------------------------------------------------------------
 
-__device__ __forceinline__ uint32_t pair_count(const PairRec *recs, uint32_t p)
+__device__ __forceinline__ uint32_t rect_count(uint64_t w)
 {
-    return recs[p].cf & kCountMask;
+    return static_cast<uint32_t>((w >> 16) & 0xFFFFu) * static_cast<uint32_t>(w >> 48);
 }
 
 // per-CTA sums of the tile counts of its chunk of sorted pairs
-__global__ void __launch_bounds__(kThreads) k_count_sums(const uint32_t *__restrict__ sorted,
+__global__ void __launch_bounds__(kThreads) k_count_sums(const uint64_t *__restrict__ srect,
                                                          int64_t n_total, const uint32_t *n_valid,
-                                                         const PairRec *__restrict__ recs,
                                                          uint32_t *__restrict__ block_sums)
 {
     __shared__ unsigned long long s_sum[kWarps];
@@ -228,7 +229,7 @@ __global__ void __launch_bounds__(kThreads) k_count_sums(const uint32_t *__restr
     const int64_t b = chunk * blockIdx.x;
     const int64_t e = b + chunk < n ? b + chunk : n;
     unsigned long long sum = 0;
-    for (int64_t j = b + threadIdx.x; j < e; j += kThreads) sum += pair_count(recs, sorted[j]);
+    for (int64_t j = b + threadIdx.x; j < e; j += kThreads) sum += rect_count(srect[j]);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xFFFFFFFFu, sum, o);
     if ((threadIdx.x & 31) == 0) s_sum[threadIdx.x >> 5] = sum;
@@ -296,31 +297,42 @@ __global__ void __launch_bounds__(1024) k_scan_sums(uint32_t *__restrict__ block
     }
 }
 
-// each thread emits the tiles of consecutive sorted pairs; offsets from a CTA scan
+// Emission: each CTA takes its chunk of sorted pairs 256 at a time, reading the pair ids and
+// their tile rectangles in sorted order; a CTA scan of the tile counts gives every pair its run
+// of output entries, and then each thread writes one entry at a time -- consecutive threads,
+// consecutive entries -- finding its pair by binary search over the run ends.  Entry k of a
+// pair with tile columns tc0 .. tc0 + ntc - 1 (mod tiles_c) and first tile row tr0 is tile row
+// tr0 + k / ntc, column tc0 + k % ntc: row-major over the pair's tile rectangle.
 __global__ void __launch_bounds__(kThreads) k_emit(
-    const uint32_t *__restrict__ sorted, int64_t n_total, const uint32_t *n_valid,
-    const PairRec *__restrict__ recs,
-    const ViewDesc *__restrict__ views, int64_t n_per_view, int tile_h, int tile_w,
+    const uint32_t *__restrict__ sorted, const uint64_t *__restrict__ srect, int64_t n_total,
+    const uint32_t *n_valid, const ViewDesc *__restrict__ views, int64_t n_per_view,
     const uint32_t *__restrict__ block_base, uint32_t *__restrict__ tile_keys,
     uint32_t *__restrict__ tile_vals, int64_t max_pairs)
 {
     __shared__ uint32_t s_warp[kWarps];
     __shared__ uint32_t s_carry;
+    __shared__ uint32_t s_end[kThreads];    // end of each pair's run inside the batch
+    __shared__ uint32_t s_p[kThreads];      // pair id
+    __shared__ uint32_t s_row0[kThreads];   // global id of the tile (first tile row, column 0)
+    __shared__ int s_tc0[kThreads], s_ntc[kThreads], s_tilesc[kThreads];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int64_t n = clamp_count(n_valid, n_total);
     const int64_t chunk = (n + gridDim.x - 1) / gridDim.x;
     const int64_t b = chunk * blockIdx.x;
     const int64_t e = b + chunk < n ? b + chunk : n;
+    const uint32_t npv = static_cast<uint32_t>(n_per_view);
     if (tid == 0) s_carry = block_base[blockIdx.x];
     __syncthreads();
     for (int64_t base = b; base < e; base += kThreads) {
         const int64_t j = base + tid;
         uint32_t p = 0, cnt = 0;
+        uint64_t w = 0;
         if (j < e) {
             p = sorted[j];
-            cnt = pair_count(recs, p);
+            w = srect[j];
+            cnt = rect_count(w);
         }
-        // block exclusive scan of cnt
+        // block inclusive scan of cnt
         uint32_t x = cnt;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
@@ -328,32 +340,44 @@ __global__ void __launch_bounds__(kThreads) k_emit(
             if (lane >= o) x += y;
         }
         if (lane == 31) s_warp[warp] = x;
+        if (cnt) {
+            const ViewDesc &vd = views[p / npv];
+            s_row0[tid] = static_cast<uint32_t>(vd.tile_offset +
+                                                static_cast<int64_t>(w & 0xFFFFu) * vd.tiles_c);
+            s_tc0[tid] = static_cast<int>((w >> 32) & 0xFFFFu);
+            s_ntc[tid] = static_cast<int>(w >> 48);
+            s_tilesc[tid] = vd.tiles_c;
+        }
+        s_p[tid] = p;
         __syncthreads();
         uint32_t wbase = 0, total = 0;
 #pragma unroll
-        for (int w = 0; w < kWarps; ++w) {
-            const uint32_t sw = s_warp[w];
-            wbase += w < warp ? sw : 0u;
+        for (int k = 0; k < kWarps; ++k) {
+            const uint32_t sw = s_warp[k];
+            wbase += k < warp ? sw : 0u;
             total += sw;
         }
-        const uint32_t off = s_carry + wbase + x - cnt;
-        if (cnt) {
-            const int v = static_cast<int>(p / n_per_view);
-            const ViewDesc &vd = views[v];
-            const PairRec rec = recs[p];
-            int tc0, ntc;
-            tile_cols_of(rec.c0, rec.nc, vd.cols, tile_w, vd.tiles_c, &tc0, &ntc);
-            const int tr0 = rec.r0 / tile_h, tr1 = rec.r1 / tile_h;
-            uint32_t k = 0;
-            for (int tr = tr0; tr <= tr1; ++tr) {
-                for (int c = 0; c < ntc; ++c, ++k) {
-                    const uint64_t o = static_cast<uint64_t>(off) + k;
-                    if (o >= static_cast<uint64_t>(max_pairs)) continue;
-                    int tc = tc0 + c;
-                    tc = tc >= vd.tiles_c ? tc - vd.tiles_c : tc;
-                    tile_keys[o] = static_cast<uint32_t>(vd.tile_offset + tr * vd.tiles_c + tc);
-                    tile_vals[o] = p;
-                }
+        s_end[tid] = wbase + x;
+        __syncthreads();
+        const uint64_t carry = s_carry;
+        for (uint32_t q = tid; q < total; q += kThreads) {
+            int lo = 0, hi = kThreads - 1;   // first pair whose run ends after q
+#pragma unroll
+            for (int step = 0; step < 8; ++step) {
+                const int mid = (lo + hi) >> 1;
+                if (s_end[mid] > q) hi = mid; else lo = mid + 1;
+            }
+            const uint32_t k = q - (lo ? s_end[lo - 1] : 0u);
+            const uint32_t ntc = static_cast<uint32_t>(s_ntc[lo]);
+            const uint32_t row = k / ntc;
+            int tc = s_tc0[lo] + static_cast<int>(k - row * ntc);
+            const int tiles_c = s_tilesc[lo];
+            tc = tc >= tiles_c ? tc - tiles_c : tc;
+            const uint64_t o = carry + q;
+            if (o < static_cast<uint64_t>(max_pairs)) {
+                tile_keys[o] = s_row0[lo] + row * static_cast<uint32_t>(tiles_c) +
+                               static_cast<uint32_t>(tc);
+                tile_vals[o] = s_p[lo];
             }
         }
         __syncthreads();
@@ -427,7 +451,8 @@ cudaError_t launch_order_tiles(const uint2 *ranges, int64_t n_tiles, uint32_t *o
 cudaError_t radix_sort_pairs(uint32_t *keys, uint32_t *vals, uint32_t *keys_alt, uint32_t *vals_alt,
                              const uint32_t *d_count, int64_t max_n, int bits, uint32_t *tmp_hist,
                              uint32_t **keys_out, uint32_t **vals_out, cudaStream_t st,
-                             const uint32_t *d_count_kept)
+                             const uint32_t *d_count_kept, const uint64_t *aux_in,
+                             uint64_t *aux_out)
 {
     uint32_t *kin = keys, *vin = vals, *kout = keys_alt, *vout = vals_alt;
     if (max_n > 0) {
@@ -439,8 +464,10 @@ cudaError_t radix_sort_pairs(uint32_t *keys, uint32_t *vals, uint32_t *keys_alt,
             const uint32_t *cnt = d_count_kept && shift > 0 ? d_count_kept : d_count;
             k_upsweep<<<kSortGrid, kThreads, 0, st>>>(kin, cnt, max_n, shift, drop, tmp_hist);
             k_scan_digits<<<kRadix / 8, 256, 0, st>>>(tmp_hist, kSortGrid, dtot);
+            const bool last = shift + 8 >= bits;
             k_downsweep<<<kSortGrid, kThreads, 0, st>>>(kin, vin, kout, vout, cnt, max_n, shift,
-                                                        drop, tmp_hist, dtot);
+                                                        drop, tmp_hist, dtot, aux_in,
+                                                        last ? aux_out : nullptr);
             uint32_t *t = kin;
             kin = kout;
             kout = t;
@@ -454,18 +481,16 @@ cudaError_t radix_sort_pairs(uint32_t *keys, uint32_t *vals, uint32_t *keys_alt,
     return cudaGetLastError();
 }
 
-cudaError_t launch_emit(const uint32_t *sorted_pair_ids, int64_t n_pairs_total,
-                        const uint32_t *n_valid, const PairRec *recs, const ViewDesc *views,
-                        int64_t n_per_view, int tile_h, int tile_w, uint32_t *block_sums,
-                        uint32_t *tile_keys, uint32_t *tile_vals, int64_t max_pairs,
-                        uint32_t *d_count, uint32_t *status, cudaStream_t st)
+cudaError_t launch_emit(const uint32_t *sorted_pair_ids, const uint64_t *sorted_trect,
+                        int64_t n_pairs_total, const uint32_t *n_valid, const ViewDesc *views,
+                        int64_t n_per_view, uint32_t *block_sums, uint32_t *tile_keys,
+                        uint32_t *tile_vals, int64_t max_pairs, uint32_t *d_count,
+                        uint32_t *status, cudaStream_t st)
 {
-    k_count_sums<<<kScanGrid, kThreads, 0, st>>>(sorted_pair_ids, n_pairs_total, n_valid, recs,
-                                                  block_sums);
+    k_count_sums<<<kScanGrid, kThreads, 0, st>>>(sorted_trect, n_pairs_total, n_valid, block_sums);
     k_scan_sums<<<1, 1024, 0, st>>>(block_sums, kScanGrid, max_pairs, d_count, status);
-    k_emit<<<kScanGrid, kThreads, 0, st>>>(sorted_pair_ids, n_pairs_total, n_valid, recs, views,
-                                           n_per_view,
-                                           tile_h, tile_w, block_sums, tile_keys, tile_vals,
+    k_emit<<<kScanGrid, kThreads, 0, st>>>(sorted_pair_ids, sorted_trect, n_pairs_total, n_valid,
+                                           views, n_per_view, block_sums, tile_keys, tile_vals,
                                            max_pairs);
     return cudaGetLastError();
 }
