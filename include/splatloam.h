@@ -374,7 +374,7 @@ SPLAT_API int splat_refine_step(splat_ctx *ctx, float *pos_logit, float *quat, f
  * device memory (for instance a process whose device memory is owned by another allocator, or
  * code that must not call cudaMalloc once it is running).  It renders one view like
  * splat_render, with no context: every workspace buffer lives in one array of the library
- * (about 7 MB, held on every device that loads the library until the process exits), and the
+ * (about 8 MB, held on every device that loads the library until the process exits), and the
  * call allocates nothing -- no cudaMalloc, cudaFree or host heap.
  * Limits: g->n <= 16384 primitives, rows <= 256, rows * cols <= 65536 pixels, at most 4096
  * tiles and 262144 (tile, primitive) pairs.  cfg = NULL uses splat_default_config.
