@@ -361,7 +361,10 @@ def run_ours(args):
     achieved = k_ev * OPS_PER_EVAL[dom] / (k_ms * 1e-3) / 1e12
     roofline = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": peak_tops,
                 "unit": "TFLOP/s", "frac": achieved / peak_tops,
-                "traffic": recorded_traffic(dom, f"{tile[0]}x{tile[1]}"),
+                # the committed capture covers the default workload only
+                "traffic": (recorded_traffic(dom, f"{tile[0]}x{tile[1]}")
+                            if args.workload == 3 and args.n_gaussians is None
+                            and args.keyframes is None else None),
                 "peak_source": (f"{sms} SMs x {FP32_LANES_PER_SM} FP32 lanes x {f_max / 1e6:.0f} "
                                 f"MHz ({peak_src} max SM clock), one op per lane per clock"),
                 "ops_per_eval": OPS_PER_EVAL[dom], "evals_per_launch": k_ev,
