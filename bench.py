@@ -378,11 +378,11 @@ def run_ours(args):
     hbm = float(peaks.get("hbm_gbs", 6800.0))
     n, V, nv, M, T = scene.n, len(views), s2["n_touching"], s2["n_pairs"], s2["n_tiles"]
     passes = (max(int(T - 1).bit_length(), 1) + 7) // 8
-    stage_bytes = {"projection": 40 * n + 32 * n * V,
+    stage_bytes = {"projection": 40 * n + 40 * n * V,
                    "range sort": 12 * n * V + 84 * nv,
                    "emission": 20 * nv + 8 * M,
                    "tile sort": 20 * passes * M,
-                   "tile ranges": 29 * M + 20 * T,
+                   "tile ranges": 21 * M + 20 * T,
                    "loss": 52 * pixels,
                    "fused Adam": 304 * n}
     stages = {}

@@ -87,6 +87,7 @@ struct splat_ctx {
     PairRec *d_recs = nullptr;
     uint32_t *d_dkeys = nullptr, *d_dvals = nullptr, *d_dkeys2 = nullptr, *d_dvals2 = nullptr;
     uint64_t *d_trect = nullptr, *d_srect = nullptr;   // pair tile rectangles, and in range order
+    uint64_t *d_prect = nullptr;   // pair pixel rectangles with the normal-flip bit
     uint32_t *d_tkeys = nullptr, *d_tvals = nullptr, *d_tkeys2 = nullptr, *d_tvals2 = nullptr;
     uint32_t *d_block_sums = nullptr, *d_hist = nullptr;
     uint2 *d_ranges = nullptr;
@@ -219,7 +220,8 @@ int render_core(splat_ctx *ctx, const splat_gaussians *g, float *depth, float *n
                              reinterpret_cast<const float2 *>(g->log_scale), n, ctx->d_views,
                              ctx->n_views, ctx->cfg.sigma_cut, ctx->cfg.alpha_min, th, tw,
                              ctx->cfg.flip_normals,
-                             ctx->d_recs, ctx->d_dkeys, ctx->d_dvals, ctx->d_trect, cnt + 1,
+                             ctx->d_recs, ctx->d_dkeys, ctx->d_dvals, ctx->d_trect,
+                             ctx->d_prect, cnt + 1,
                              cnt + 4, st,
                              active));
     CK(stage_mark(1));
@@ -242,7 +244,7 @@ int render_core(splat_ctx *ctx, const splat_gaussians *g, float *depth, float *n
     // blocks each meets
     uint32_t *rects = tv == ctx->d_tvals ? ctx->d_tvals2 : ctx->d_tvals;
     uint8_t *blocks = reinterpret_cast<uint8_t *>(tk == ctx->d_tkeys ? ctx->d_tkeys2 : ctx->d_tkeys);
-    CK(splat::launch_ranges(tk, tv, ctx->d_recs, ctx->d_tileinfo, th, tw, cnt,
+    CK(splat::launch_ranges(tk, tv, ctx->d_prect, ctx->d_tileinfo, th, tw, cnt,
                             ctx->cap.max_pairs, ctx->d_ranges, ctx->n_tiles, rects, blocks, st));
     CK(splat::launch_order_tiles(ctx->d_ranges, ctx->n_tiles, ctx->d_tile_order, st));
     CK(stage_mark(5));
@@ -303,7 +305,7 @@ int backward_core(splat_ctx *ctx, const splat_gaussians *g, const float *gD, con
 void free_ctx(splat_ctx *c)
 {
     void *ptrs[] = {c->d_views, c->d_frames, c->d_tile_view, c->d_recs, c->d_dkeys, c->d_dvals,
-                    c->d_dkeys2, c->d_dvals2, c->d_trect, c->d_srect, c->d_tkeys, c->d_tvals, c->d_tkeys2, c->d_tvals2,
+                    c->d_dkeys2, c->d_dvals2, c->d_trect, c->d_srect, c->d_prect, c->d_tkeys, c->d_tvals, c->d_tkeys2, c->d_tvals2,
                     c->d_block_sums, c->d_hist, c->d_ranges, c->d_tfinal, c->d_nlast, c->d_wgrad,
                     c->d_pose, c->d_rec, c->d_rec_prev, c->d_rec_head, c->d_rec_fill,
                     c->d_samp_thr, c->d_active, c->d_grow_sums,
@@ -395,6 +397,7 @@ SPLAT_API int splat_ctx_create(const splat_render_config *cfg, const splat_capac
     if (e == cudaSuccess) e = dalloc(&c->d_dvals2, mpv);
     if (e == cudaSuccess) e = dalloc(&c->d_trect, mpv);
     if (e == cudaSuccess) e = dalloc(&c->d_srect, mpv);
+    if (e == cudaSuccess) e = dalloc(&c->d_prect, mpv);
     if (e == cudaSuccess) e = dalloc(&c->d_tkeys, M);
     if (e == cudaSuccess) e = dalloc(&c->d_tvals, M);
     if (e == cudaSuccess) e = dalloc(&c->d_tkeys2, M);

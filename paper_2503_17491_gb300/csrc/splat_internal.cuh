@@ -184,6 +184,28 @@ __host__ __device__ inline void tile_cols_of(int c0, int nc, int cols, int tw, i
     *ntc = n;
 }
 
+// A pair's pixel rectangle and normal-flip bit in one word: r0 | flip << 15, r1, c0, nc, 16 bits
+// each (rows and columns are below 2^15)
+__host__ __device__ inline uint64_t pack_pixel_rect(const PairRec &rec)
+{
+    const uint32_t r0 = static_cast<uint16_t>(rec.r0) | ((rec.cf & kPairFlip) ? 0x8000u : 0u);
+    return static_cast<uint64_t>(r0) | static_cast<uint64_t>(static_cast<uint16_t>(rec.r1)) << 16 |
+           static_cast<uint64_t>(static_cast<uint16_t>(rec.c0)) << 32 |
+           static_cast<uint64_t>(static_cast<uint16_t>(rec.nc)) << 48;
+}
+
+__host__ __device__ inline PairRec unpack_pixel_rect(uint64_t w)
+{
+    PairRec rec;
+    rec.r0 = static_cast<int16_t>(w & 0x7FFFu);
+    rec.r1 = static_cast<int16_t>((w >> 16) & 0xFFFFu);
+    rec.c0 = static_cast<int16_t>((w >> 32) & 0xFFFFu);
+    rec.nc = static_cast<int16_t>(w >> 48);
+    rec.kappa = 0.0f;
+    rec.cf = (w & 0x8000u) ? kPairFlip : 0u;
+    return rec;
+}
+
 // A pair's tile rectangle in one word: first tile row, tile rows, first tile column, tile columns
 // (cyclic modulo the view's tile columns), 16 bits each; every field is below 2^13 for images
 // of at most 32,767 rows and columns and tiles of at least 4 pixels a side.
@@ -309,12 +331,13 @@ __device__ __forceinline__ void chain_params(const float4 pl, const float4 q, co
 // ---------------------------------------------------------------------------------------------
 struct Workspace;   // host-side bookkeeping, defined in splat_abi.cu
 
-// trect[p]: the pair's tile rectangle as one word (see pack_tile_rect), 0 when it touches none
+// trect[p]: the pair's tile rectangle as one word (see pack_tile_rect), 0 when it touches none;
+// prect[p]: its pixel rectangle and normal-flip bit (pack_pixel_rect)
 cudaError_t launch_project(const float4 *pos_logit, const float4 *quat, const float2 *log_scale,
                            int64_t n, const ViewDesc *views, int n_views, float sigma,
                            float alpha_min, int tile_h, int tile_w, int flip_normals,
                            PairRec *recs, uint32_t *dkeys, uint32_t *dvals, uint64_t *trect,
-                           uint32_t *status, uint32_t *n_valid, cudaStream_t st,
+                           uint64_t *prect, uint32_t *status, uint32_t *n_valid, cudaStream_t st,
                            const uint8_t *active = nullptr);
 
 // stable LSD radix sort of (uint32 key, uint32 value) pairs on key bits [0, bits);
@@ -413,7 +436,7 @@ __device__ __forceinline__ uint32_t rect_blocks(uint32_t rect, int tile_h, int t
 // inside its tile (tile_local_rect) in entry_rect and the 4 x 8 blocks it meets (rect_blocks) in
 // entry_blocks
 cudaError_t launch_ranges(const uint32_t *tile_keys, const uint32_t *tile_vals,
-                          const PairRec *recs, const TileInfo *tiles, int tile_h, int tile_w,
+                          const uint64_t *prect, const TileInfo *tiles, int tile_h, int tile_w,
                           const uint32_t *d_count, int64_t max_pairs, uint2 *ranges,
                           int64_t n_tiles, uint32_t *entry_rect, uint8_t *entry_blocks,
                           cudaStream_t st);

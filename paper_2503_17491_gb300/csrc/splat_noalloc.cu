@@ -46,7 +46,8 @@ constexpr size_t kOffDkeys2 = align256(kOffDvals + 4 * kMaxGaussians);
 constexpr size_t kOffDvals2 = align256(kOffDkeys2 + 4 * kMaxGaussians);
 constexpr size_t kOffTrect = align256(kOffDvals2 + 4 * kMaxGaussians);
 constexpr size_t kOffSrect = align256(kOffTrect + 8 * kMaxGaussians);
-constexpr size_t kOffTkeys = align256(kOffSrect + 8 * kMaxGaussians);
+constexpr size_t kOffPrect = align256(kOffSrect + 8 * kMaxGaussians);
+constexpr size_t kOffTkeys = align256(kOffPrect + 8 * kMaxGaussians);
 constexpr size_t kOffTvals = align256(kOffTkeys + 4 * kMaxPairs);
 constexpr size_t kOffTkeys2 = align256(kOffTvals + 4 * kMaxPairs);
 constexpr size_t kOffTvals2 = align256(kOffTkeys2 + 4 * kMaxPairs);
@@ -246,6 +247,7 @@ extern "C" SPLAT_API int splat_render_noalloc(const splat_gaussians *g,
     uint32_t *dvals2 = reinterpret_cast<uint32_t *>(base + kOffDvals2);
     uint64_t *trect = reinterpret_cast<uint64_t *>(base + kOffTrect);
     uint64_t *srect = reinterpret_cast<uint64_t *>(base + kOffSrect);
+    uint64_t *prect = reinterpret_cast<uint64_t *>(base + kOffPrect);
     uint32_t *tkeys = reinterpret_cast<uint32_t *>(base + kOffTkeys);
     uint32_t *tvals = reinterpret_cast<uint32_t *>(base + kOffTvals);
     uint32_t *tkeys2 = reinterpret_cast<uint32_t *>(base + kOffTkeys2);
@@ -275,7 +277,7 @@ extern "C" SPLAT_API int splat_render_noalloc(const splat_gaussians *g,
                                 reinterpret_cast<const float4 *>(g->quat_wxyz),
                                 reinterpret_cast<const float2 *>(g->log_scale), n, view, 1,
                                 cfg.sigma_cut, cfg.alpha_min, th, tw, cfg.flip_normals, recs, dkeys,
-                                dvals, trect, cnt + 1, cnt + 4, st));
+                                dvals, trect, prect, cnt + 1, cnt + 4, st));
     uint32_t *dk, *dv;
     NA_CK(splat::radix_sort_pairs(dkeys, dvals, dkeys2, dvals2, nullptr, n, 32, hist, &dk, &dv, st,
                                   nullptr, trect, srect));
@@ -286,7 +288,7 @@ extern "C" SPLAT_API int splat_render_noalloc(const splat_gaussians *g,
                                   hist, &tk, &tv, st));
     uint32_t *rects = tv == tvals ? tvals2 : tvals;   // the tile sort's free buffers
     uint8_t *blocks = reinterpret_cast<uint8_t *>(tk == tkeys ? tkeys2 : tkeys);
-    NA_CK(splat::launch_ranges(tk, tv, recs, tiles, th, tw, cnt, kMaxPairs, ranges, n_tiles, rects,
+    NA_CK(splat::launch_ranges(tk, tv, prect, tiles, th, tw, cnt, kMaxPairs, ranges, n_tiles, rects,
                                blocks, st));
     NA_CK(splat::launch_order_tiles(ranges, n_tiles, order, st));
 

@@ -271,7 +271,7 @@ __global__ void __launch_bounds__(256) k_project(
     const float2 *__restrict__ log_scale, int64_t n, const ViewDesc *__restrict__ views,
     int n_views, float sigma, float alpha_min, int tile_h, int tile_w, int flip_normals,
     PairRec *__restrict__ recs, uint32_t *__restrict__ dkeys, uint32_t *__restrict__ dvals,
-    uint64_t *__restrict__ trect, uint32_t *__restrict__ status,
+    uint64_t *__restrict__ trect, uint64_t *__restrict__ prect, uint32_t *__restrict__ status,
     uint32_t *__restrict__ n_valid, const uint8_t *__restrict__ active)
 {
     const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
@@ -343,6 +343,7 @@ __global__ void __launch_bounds__(256) k_project(
         }
         recs[p] = rec;
         trect[p] = (rec.cf & kCountMask) ? tr : 0ull;
+        prect[p] = pack_pixel_rect(rec);
         dkeys[p] = (rec.cf & kCountMask) ? __float_as_uint(rec.kappa) : 0xFFFFFFFFu;
         dvals[p] = static_cast<uint32_t>(p);
         nv += (rec.cf & kCountMask) ? 1u : 0u;
@@ -360,14 +361,14 @@ cudaError_t launch_project(const float4 *pos_logit, const float4 *quat, const fl
                            int64_t n, const ViewDesc *views, int n_views, float sigma,
                            float alpha_min, int tile_h, int tile_w, int flip_normals,
                            PairRec *recs, uint32_t *dkeys, uint32_t *dvals, uint64_t *trect,
-                           uint32_t *status, uint32_t *n_valid, cudaStream_t st,
+                           uint64_t *prect, uint32_t *status, uint32_t *n_valid, cudaStream_t st,
                            const uint8_t *active)
 {
     if (n <= 0) return cudaSuccess;
     const unsigned grid = static_cast<unsigned>((n + 255) / 256);
     k_project<<<grid, 256, 0, st>>>(pos_logit, quat, log_scale, n, views, n_views, sigma,
                                     alpha_min, tile_h, tile_w, flip_normals, recs, dkeys, dvals,
-                                    trect, status, n_valid, active);
+                                    trect, prect, status, n_valid, active);
     return cudaGetLastError();
 }
 

@@ -390,7 +390,7 @@ __global__ void __launch_bounds__(kThreads) k_emit(
 // rectangle inside its tile, so that the renderer's warps (eight per tile) need not each gather
 // the record and clip it
 __global__ void k_ranges(const uint32_t *__restrict__ keys, const uint32_t *__restrict__ vals,
-                         const PairRec *__restrict__ recs, const TileInfo *__restrict__ tiles,
+                         const uint64_t *__restrict__ prect, const TileInfo *__restrict__ tiles,
                          int tile_h, int tile_w, const uint32_t *d_count, int64_t max_pairs,
                          uint2 *__restrict__ ranges, uint32_t *__restrict__ entry_rect,
                          uint8_t *__restrict__ entry_blocks)
@@ -402,7 +402,8 @@ __global__ void k_ranges(const uint32_t *__restrict__ keys, const uint32_t *__re
         if (j == 0 || keys[j - 1] != t) ranges[t].x = static_cast<uint32_t>(j);
         if (j == m - 1 || keys[j + 1] != t) ranges[t].y = static_cast<uint32_t>(j + 1);
         const TileInfo &ti = tiles[t];
-        const uint32_t r = tile_local_rect(recs[vals[j]], ti.tr, ti.tc, ti.cols, tile_h, tile_w);
+        const uint32_t r = tile_local_rect(unpack_pixel_rect(prect[vals[j]]), ti.tr, ti.tc,
+                                           ti.cols, tile_h, tile_w);
         entry_rect[j] = r;
         entry_blocks[j] = static_cast<uint8_t>(rect_blocks(r & ~kRectFlip, tile_h, tile_w));
     }
@@ -496,14 +497,14 @@ cudaError_t launch_emit(const uint32_t *sorted_pair_ids, const uint64_t *sorted_
 }
 
 cudaError_t launch_ranges(const uint32_t *tile_keys, const uint32_t *tile_vals,
-                          const PairRec *recs, const TileInfo *tiles, int tile_h, int tile_w,
+                          const uint64_t *prect, const TileInfo *tiles, int tile_h, int tile_w,
                           const uint32_t *d_count, int64_t max_pairs, uint2 *ranges,
                           int64_t n_tiles, uint32_t *entry_rect, uint8_t *entry_blocks,
                           cudaStream_t st)
 {
     cudaError_t e = cudaMemsetAsync(ranges, 0, sizeof(uint2) * static_cast<size_t>(n_tiles), st);
     if (e != cudaSuccess) return e;
-    k_ranges<<<kRangesGrid, 256, 0, st>>>(tile_keys, tile_vals, recs, tiles, tile_h, tile_w,
+    k_ranges<<<kRangesGrid, 256, 0, st>>>(tile_keys, tile_vals, prect, tiles, tile_h, tile_w,
                                             d_count, max_pairs, ranges, entry_rect,
                                             entry_blocks);
     return cudaGetLastError();
