@@ -417,6 +417,36 @@ def adam_step(params, grads, state, cfg: AdamConfig | None = None, stream=None):
                                    _stream(stream)), "splat_adam_step")
 
 
+def save_checkpoint(path, params, state, extra=None):
+    """Write the map parameters (pos_logit, quat, log_scale), the Adam moments and step count of
+    `state` (as from adam_state) and an optional dict of plain values to `path` (torch.save)."""
+    torch.save({"params": [t.detach().cpu() for t in params],
+                "state": [t.detach().cpu() for t in state],
+                "extra": dict(extra or {})}, path)
+
+
+def load_checkpoint(path, params=None, state=None, device="cuda"):
+    """Read a checkpoint written by save_checkpoint.  With `params` / `state` given (tensors of
+    the same shapes), the values are copied into them in place -- a CUDA graph captured on those
+    tensors keeps working -- otherwise new tensors are made on `device`.  Returns
+    (params, state, extra)."""
+    ck = torch.load(path, map_location="cpu")
+
+    def fill(saved, dst):
+        if dst is None:
+            return tuple(t.to(device) for t in saved)
+        if len(dst) != len(saved):
+            raise ValueError("checkpoint holds %d tensors, %d given" % (len(saved), len(dst)))
+        for t, v in zip(dst, saved):
+            if t.shape != v.shape or t.dtype != v.dtype:
+                raise ValueError(f"checkpoint tensor {tuple(v.shape)} {v.dtype} does not fit "
+                                 f"{tuple(t.shape)} {t.dtype}")
+            t.copy_(v)
+        return tuple(dst)
+
+    return fill(ck["params"], params), fill(ck["state"], state), ck["extra"]
+
+
 class SplatRender(torch.autograd.Function):
     """(pos_logit, quat, log_scale) -> (depth (P,), normal (3,P), alpha (P,)) for the views
     registered in the context; gradients through splat_render_views_backward."""
@@ -514,6 +544,17 @@ class Refiner:
         else:
             self._plain_step()
         return self.loss_out
+
+    def save(self, path):
+        """Checkpoint the map and the optimiser state (save_checkpoint)."""
+        torch.cuda.synchronize()
+        save_checkpoint(path, self.params, self.state, {"n": self.n, "keyframes": len(self.views)})
+
+    def load(self, path):
+        """Resume from a checkpoint of a refiner of the same map size, in place (a captured
+        graph stays valid)."""
+        torch.cuda.synchronize()
+        load_checkpoint(path, self.params, self.state)
 
 
 def default_capacity_pairs(n, views, per_prim=24):
