@@ -602,12 +602,19 @@ class Mapper:
     first keyframe, the densification masks M_n / M_e against a render of the current map for
     later ones), then refinement iterations (splat_refine_step) run over the registered keyframes
     with keyframe sampling (splat_set_view_sampling).  The parameters and Adam moments live in
-    tensors of a fixed capacity; the first `n` rows are the map."""
+    tensors of a fixed capacity; the first `n` rows are the map.  With max_keyframes set, only
+    the most recent keyframes stay registered (a sliding window, as in a long run that refines
+    over the last few keyframes of each scan); max_views and max_pixels then need to hold the
+    window only."""
 
     def __init__(self, capacity: int, max_views: int, max_pixels: int, n_new: int,
                  cfg: RenderConfig | None = None, loss_cfg: LossConfig | None = None,
                  adam_cfg: AdamConfig | None = None, densify_cfg: DensifyConfig | None = None,
-                 draws: int = 2, p_newest: float = 0.4, seed: int = 0, device="cuda"):
+                 draws: int = 2, p_newest: float = 0.4, seed: int = 0, device="cuda",
+                 max_keyframes: int | None = None):
+        if max_keyframes is not None and not 1 <= int(max_keyframes) <= int(max_views):
+            raise ValueError("max_keyframes must lie in [1, max_views]")
+        self.max_keyframes = None if max_keyframes is None else int(max_keyframes)
         self.capacity, self.n_new = int(capacity), int(n_new)
         self.draws, self.p_newest, self.seed = int(draws), float(p_newest), int(seed)
         self.loss_cfg = loss_cfg or LossConfig(lambda_n=0.1, normal_mode=1)
@@ -619,6 +626,7 @@ class Mapper:
         self.state = adam_state(self.capacity, dev)
         self.n = 0
         self.views: list = []
+        self.targets: list = []   # (depth (P,), normal (3, P)) of each registered keyframe
         self.t_depth = torch.zeros(0, device=dev)
         self.t_normal = torch.zeros(3, 0, device=dev)
         self.loss_out = torch.zeros(1, dtype=torch.float64, device=dev)
@@ -631,12 +639,16 @@ class Mapper:
         from it by n_new slots and return the map size."""
         if self.n + self.n_new > self.capacity:
             raise ValueError("map capacity exhausted")
-        self.views.append(view)
-        self.ctx.set_views(self.views)
         td = target_depth.reshape(-1).to(self.t_depth.device, torch.float32)
         tn = target_normal.reshape(3, -1).to(self.t_depth.device, torch.float32)
-        self.t_depth = torch.cat([self.t_depth, td]).contiguous()
-        self.t_normal = torch.cat([self.t_normal, tn], 1).contiguous()
+        self.views.append(view)
+        self.targets.append((td, tn))
+        if self.max_keyframes is not None and len(self.views) > self.max_keyframes:
+            del self.views[0]
+            del self.targets[0]
+        self.ctx.set_views(self.views)
+        self.t_depth = torch.cat([t[0] for t in self.targets]).contiguous()
+        self.t_normal = torch.cat([t[1] for t in self.targets], 1).contiguous()
         # only the new keyframe's pixels are drawn from
         only_new = torch.zeros_like(self.t_depth)
         o = self.ctx.offsets[-1]

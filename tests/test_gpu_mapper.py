@@ -55,3 +55,39 @@ def test_mapper_grows_and_refines_a_street():
         cov, err = _range_stats(mapper, k, dt)
         print("keyframe", k, "coverage", cov, "median range error", err)
         assert cov > 0.95 and err < 0.15
+
+
+def test_mapper_keeps_a_window_of_recent_keyframes():
+    """With max_keyframes, only the most recent keyframes stay registered: the map keeps growing
+    with every keyframe while refinement runs over the window, and the window's scans end up
+    covered by the map."""
+    s = scenes.workload(3, n=1000)
+    views = s.views[:6]
+    targets = [scenes.render_targets(s, v) for v in views]
+    window = 3
+    P = max(sum(v.rows * v.cols for v in views[k:k + window]) for k in range(len(views)))
+    n_new = 10_000
+    mapper = api.Mapper(capacity=n_new * len(views), max_views=window, max_pixels=P,
+                        n_new=n_new, max_keyframes=window,
+                        loss_cfg=api.LossConfig(lambda_n=0.1, lambda_o=0.1, normal_mode=1,
+                                                lambda_s=0.01, tau_s=0.5),
+                        densify_cfg=api.DensifyConfig(scale_k=2.0, opacity=0.6, seed=3),
+                        draws=2, seed=5)
+    for k, (v, (dt, nt)) in enumerate(zip(views, targets)):
+        mapper.add_keyframe(v, torch.from_numpy(dt).cuda(), torch.from_numpy(nt).cuda())
+        assert mapper.n == (k + 1) * n_new
+        assert len(mapper.views) == min(k + 1, window)
+        assert mapper.views[-1] is v
+        newest = len(mapper.views) - 1
+        cov0, err0 = _range_stats(mapper, newest, dt)
+        # each iteration's loss covers the keyframes drawn for it, so the losses of different
+        # iterations are not compared; the newest keyframe's rendered ranges must improve
+        losses = mapper.refine(30)
+        cov1, err1 = _range_stats(mapper, newest, dt)
+        assert mapper.ctx.status() == 0
+        assert np.isfinite(losses).all()
+        assert cov1 >= cov0 - 0.02 and err1 < err0
+    for j, (dt, _) in enumerate(targets[-window:]):
+        cov, err = _range_stats(mapper, j, dt)
+        print("window keyframe", j, "coverage", cov, "median range error", err)
+        assert cov > 0.9 and err < 0.2
