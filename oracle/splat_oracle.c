@@ -41,7 +41,7 @@
  * Readings where the paper is silent (the image grid, cutoffs, normal frame and
  * sign, parametrisation) are listed with the tests that pin them; in short:
  *   column c has azimuth  pi - 2 pi (c + 1/2) / W,
- *   row r has elevation   elev_max - r (elev_max - elev_min) / (H - 1),
+ *   row r has elevation   elev_max - r (elev_max - elev_min) / (H - 1) (elev_max for H = 1),
  *   alpha = min(o G, alpha_max), skipped below alpha_min, stop before a primitive
  *   that would bring T below t_min, 3-sigma box test max|s_hat| <= sigma_cut,
  *   hits behind the sensor skipped, D/N/O not normalised, normals in the sensor
@@ -552,7 +552,7 @@ static void pixel_ray(int r, int c, int H, int W, double emin, double emax,
                       double *v, double *hx, double *hy)
 {
     double g = OR_PI - 2.0 * OR_PI * (c + 0.5) / W;
-    double th = emax - r * (emax - emin) / (H - 1);
+    double th = H > 1 ? emax - r * (emax - emin) / (H - 1) : emax;
     v[0] = cos(th) * cos(g); v[1] = cos(th) * sin(g); v[2] = sin(th);
     double uz[3] = { 0, 0, 1 }, t[3];
     cross3(v, uz, t);

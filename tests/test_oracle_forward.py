@@ -81,6 +81,34 @@ def test_head_on_closed_form_every_pixel(oracle_mod, L, o, sa, sb):
     assert checked > 20
 
 
+def test_single_row_image_looks_along_elev_max(oracle_mod):
+    """A one-row image has no row spacing: its rays sit at elev_max (the pixel-grid reading of
+    Supp. A's K), so every column of a head-on splat follows the closed form at that elevation."""
+    H, W = 1, 256
+    emin, emax = float(np.float32(-0.2)), float(np.float32(0.03))   # the intrinsics are binary32
+    L, o, sa, sb = 6.0, 0.8, 0.6, 0.3
+    pl, q, ls = one_splat(L, o, sa, sb)
+    out = oracle_mod.full_view(pl, q, ls, np.eye(4), H, W, emin, emax, mode="brute")
+    L64, o64 = float(pl[0, 0]), 1 / (1 + math.exp(-float(pl[0, 3])))
+    sa64, sb64 = math.exp(float(ls[0, 0])), math.exp(float(ls[0, 1]))
+    hits = 0
+    for c in range(W):
+        g = math.pi - 2 * math.pi * (c + 0.5) / W
+        v = (math.cos(emax) * math.cos(g), math.cos(emax) * math.sin(g), math.sin(emax))
+        if v[0] <= 0:
+            assert out["O"][0, c] == 0
+            continue
+        s1, s2 = L64 * v[1] / (v[0] * sa64), L64 * v[2] / (v[0] * sb64)
+        a = o64 * math.exp(-0.5 * (s1 * s1 + s2 * s2))
+        if not (max(abs(s1), abs(s2)) <= 3 and a >= 1 / 255):
+            assert out["O"][0, c] == 0
+            continue
+        assert out["D"][0, c] == pytest.approx(a * L64 / v[0], rel=1e-11)
+        assert out["O"][0, c] == pytest.approx(a, rel=1e-11)
+        hits += 1
+    assert hits >= 4
+
+
 def test_two_splats_front_to_back_closed_form(oracle_mod):
     """Two coaxial splats: D = a1 d1 + (1-a1) a2 d2, O = 1 - (1-a1)(1-a2) on the axis
     (Eqs. ab_depth, ab_opacity); the nearer one composites first whatever the input order."""
