@@ -110,8 +110,8 @@ def test_batched_views_lists_and_bitwise_equal_to_single():
         np.testing.assert_array_equal(n[:, o:o + P], n1.cpu().numpy())
 
 
-def _sampled_parity(s, views, n_rand=8192, rows_per_view=4, seed=0, label=""):
-    ctx, d, n, a = _render(s, views)
+def _sampled_parity(s, views, n_rand=8192, rows_per_view=4, seed=0, label="", tile=(16, 16)):
+    ctx, d, n, a = _render(s, views, tile)
     assert ctx.status() == 0
     rng = np.random.default_rng(seed)
     per = max(n_rand // len(views), 256)
@@ -138,16 +138,20 @@ def test_workload2_full_size_sampled():
     assert sum(x["covered"] for x in stats) > 0.5 * sum(x["pixels"] for x in stats)
 
 
-def test_workload3_full_size_batched_sampled():
-    """The batched workload at full size (500k primitives, 12 uneven views) in one call."""
+@pytest.mark.parametrize("tile", TILES)
+def test_workload3_full_size_batched_sampled(tile):
+    """The batched workload at full size (500k primitives, 12 uneven views) in one call, with
+    every tile shape the benchmark's autotuner can pick."""
     s = scenes.workload(3)
-    _sampled_parity(s, s.views, n_rand=12 * 1024, rows_per_view=2, label="workload3")
+    _sampled_parity(s, s.views, n_rand=12 * 1024, rows_per_view=2, label=f"workload3 {tile}",
+                    tile=tile)
 
 
-def test_workload3_lists_bit_exact():
+@pytest.mark.parametrize("tile", TILES)
+def test_workload3_lists_bit_exact(tile):
     s = scenes.workload(3)
-    ctx, *_ = _render(s, s.views)
-    assert check_lists(ctx, s, s.views) > 10 * s.n
+    ctx, *_ = _render(s, s.views, tile)
+    assert check_lists(ctx, s, s.views, tile) > 10 * s.n
 
 
 def test_empty_and_single():
