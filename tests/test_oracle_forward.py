@@ -252,3 +252,48 @@ def test_culled_equals_brute_workload1_sample(oracle_mod):
     for k in ("D", "O", "N", "n_contrib"):
         np.testing.assert_array_equal(a[k], b[k])
     assert (a["O"] > 0.5).mean() > 0.3
+
+
+@pytest.mark.parametrize("o,band,bits", [
+    (0.8, (0.05, 0.002, 0.0, 0.0, 0.0), (1, 2)),      # box edge and alpha_min bands
+    (0.995, (0.0, 0.0, 0.0, 0.0, 0.004), (16,)),     # alpha_max clamp band
+])
+def test_ambiguity_band_flags_follow_the_closed_form(oracle_mod, o, band, bits):
+    """The band flags that take pixels out of the GPU comparison mark exactly the pixels whose
+    decision quantity lies within the band of its threshold -- checked against the head-on
+    closed form (s_hat and alpha by hand), so the parity tests exclude no more than that."""
+    H, W = 17, 256
+    emin, emax = scenes.deg(-10), scenes.deg(10)
+    L, sa, sb = 6.0, 0.6, 0.3
+    pl, q, ls = one_splat(L, o, sa, sb)
+    out = oracle_mod.full_view(pl, q, ls, np.eye(4), H, W, emin, emax, band=band, mode="brute")
+    L64, o64 = float(pl[0, 0]), 1 / (1 + math.exp(-float(pl[0, 3])))
+    sa64, sb64 = math.exp(float(ls[0, 0])), math.exp(float(ls[0, 1]))
+    a_min, a_max, sigma = 1 / 255, 0.99, 3.0
+    flagged = {b: 0 for b in bits}
+    for r in range(H):
+        th = emax - r * (emax - emin) / (H - 1)
+        for c in range(W):
+            g = math.pi - 2 * math.pi * (c + 0.5) / W
+            v = (math.cos(th) * math.cos(g), math.cos(th) * math.sin(g), math.sin(th))
+            want = 0
+            if v[0] != 0:
+                s1, s2 = L64 * v[1] / (v[0] * sa64), L64 * v[2] / (v[0] * sb64)
+                smax = max(abs(s1), abs(s2))
+                edge = abs(abs(smax - sigma) - band[0] * sigma)
+                if 1 in bits and edge < 1e-9:
+                    continue                      # on the band's own edge: either answer
+                if abs(smax - sigma) <= band[0] * sigma:
+                    want |= 1
+                if smax <= sigma and v[0] > 0:    # in front of the sensor
+                    a_raw = o64 * math.exp(-0.5 * (s1 * s1 + s2 * s2))
+                    if abs(a_raw - a_max) <= band[4]:
+                        want |= 16
+                    a = min(a_raw, a_max)
+                    if abs(a - a_min) <= band[1]:
+                        want |= 2
+            got = int(out["band"][r, c])
+            assert got == want, (r, c, got, want)
+            for b in bits:
+                flagged[b] += bool(got & b)
+    assert all(n > 0 for n in flagged.values()), flagged
