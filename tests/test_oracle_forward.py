@@ -297,3 +297,47 @@ def test_ambiguity_band_flags_follow_the_closed_form(oracle_mod, o, band, bits):
             for b in bits:
                 flagged[b] += bool(got & b)
     assert all(n > 0 for n in flagged.values()), flagged
+
+
+def test_ambiguity_band_flags_the_stop_on_t_min(oracle_mod):
+    """Three coaxial splats of opacity 0.99: with alpha clamped at 0.99 the transmittance after
+    two of them is at least 1e-4 = t_min, and the third takes it below near the axis.  The t_min
+    band flags exactly the pixels whose running transmittance comes within the band of t_min
+    (closed form), and the pixels that cross it stop before the crossing splat."""
+    H, W = 33, 2049         # a fine grid around the axis (row 16 / column 1024 look along +x)
+    emin, emax = scenes.deg(-1.5), scenes.deg(1.5)
+    splats = [one_splat(L, 0.99, 0.5, 0.5) for L in (5.0, 8.0, 11.0)]
+    pl, q, ls = (np.concatenate(x) for x in zip(*splats))
+    band = (0.0, 0.0, 0.5, 0.0, 0.0)
+    out = oracle_mod.full_view(pl, q, ls, np.eye(4), H, W, emin, emax, band=band, mode="brute")
+    t_min, a_min = 1e-4, 1 / 255
+    flagged = stopped = stopped_in_band = 0
+    for r in range(H):
+        th = emax - r * (emax - emin) / (H - 1)
+        for c in range(W):
+            g = math.pi - 2 * math.pi * (c + 0.5) / W
+            v = (math.cos(th) * math.cos(g), math.cos(th) * math.sin(g), math.sin(th))
+            want, T, n = 0, 1.0, 0
+            if v[0] > 0:
+                for P in splats:
+                    L64 = float(P[0][0, 0])
+                    o64 = 1 / (1 + math.exp(-float(P[0][0, 3])))
+                    s64 = math.exp(float(P[2][0, 0]))
+                    s1, s2 = L64 * v[1] / (v[0] * s64), L64 * v[2] / (v[0] * s64)
+                    if max(abs(s1), abs(s2)) > 3:
+                        continue
+                    al = min(o64 * math.exp(-0.5 * (s1 * s1 + s2 * s2)), 0.99)
+                    if al < a_min:
+                        continue
+                    tt = T * (1 - al)
+                    if abs(tt - t_min) <= band[2] * t_min:
+                        want |= 4
+                    if tt < t_min:
+                        stopped += 1
+                        stopped_in_band += want != 0
+                        break
+                    T, n = tt, n + 1
+            assert int(out["band"][r, c]) == want, (r, c)
+            assert int(out["n_contrib"][r, c]) == n, (r, c)
+            flagged += want != 0
+    assert flagged > 0 and stopped > 0 and stopped_in_band > 0
