@@ -18,14 +18,19 @@ using splat::SinCos2;
 using splat::ViewDesc;
 
 namespace {
-
 thread_local char g_cuda_err[256] = "";
+}  // namespace
 
+namespace splat {
 int cuda_fail(cudaError_t e, const char *what)
 {
     std::snprintf(g_cuda_err, sizeof g_cuda_err, "%s: %s", what, cudaGetErrorString(e));
     return SPLAT_ERR_CUDA;
 }
+}  // namespace splat
+
+namespace {
+using splat::cuda_fail;
 
 #define CK(call)                                          \
     do {                                                  \

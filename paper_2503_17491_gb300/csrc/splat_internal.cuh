@@ -102,7 +102,7 @@ struct GrowArgs {
 cudaError_t launch_grow(GrowArgs a, cudaStream_t st);
 
 // Photometric residual of one view against a query range image and its Gauss-Newton normal
-// equations (Sec. 3.4): out[29] = H upper triangle (21, row-major), g (6), Huber cost, count;
+// equations (Sec. 3.3.3): out[29] = H upper triangle (21, row-major), g (6), Huber cost, count;
 // per_pixel (nullable) = 8 x P planar: r, w, J (6).  T: device binary32 3 x 4 render -> query.
 cudaError_t launch_photometric(const ViewDesc &vd, const float *depth, const float *alpha,
                                const float *qdepth, const float *T, float o_min, float delta,
@@ -333,6 +333,10 @@ struct Workspace;   // host-side bookkeeping, defined in splat_abi.cu
 
 // trect[p]: the pair's tile rectangle as one word (see pack_tile_rect), 0 when it touches none;
 // prect[p]: its pixel rectangle and normal-flip bit (pack_pixel_rect)
+// Record the text of a failed CUDA call for splat_last_cuda_error (thread-local) and return
+// SPLAT_ERR_CUDA.
+int cuda_fail(cudaError_t e, const char *what);
+
 cudaError_t launch_project(const float4 *pos_logit, const float4 *quat, const float2 *log_scale,
                            int64_t n, const ViewDesc *views, int n_views, float sigma,
                            float alpha_min, int tile_h, int tile_w, int flip_normals,

@@ -13,8 +13,11 @@
 // (sizes) or SPLAT_ERR_CAPACITY (pairs, found on the device).
 //
 // Every call shares the one array (and the host tables): calls must not overlap, neither on the
-// GPU nor from several host threads.  The first call on a device looks up the array's device
-// address (cudaGetSymbolAddress) with that device current, once per device.
+// GPU nor from several host threads.  The first call on a device is the set-up call: CUDA loads
+// the library's code on first use (lazy module loading), which is when the array and the kernels
+// it launches take their device memory, and the call looks up the array's device address
+// (cudaGetSymbolAddress) with that device current, once per device.  That call must come before
+// the device's memory is handed to another allocator and outside any stream capture.
 
 #include <cmath>
 #include <cstring>
@@ -199,9 +202,10 @@ bool supported_tile(int th, int tw)
            (th == 4 && tw == 64);
 }
 
-#define NA_CK(call)                                     \
-    do {                                                \
-        if ((call) != cudaSuccess) return SPLAT_ERR_CUDA; \
+#define NA_CK(call)                                                 \
+    do {                                                            \
+        const cudaError_t e_ = (call);                              \
+        if (e_ != cudaSuccess) return splat::cuda_fail(e_, #call);  \
     } while (0)
 
 }  // namespace
