@@ -7,7 +7,7 @@ import torch
 
 import oracle
 from paper_2503_17491_gb300 import api, scenes
-from gpu_common import (BAND, compare_grads, gpu_grads_as_oracle, make_ctx, oracle_view, to_dev)
+from gpu_common import (BAND, BAND_CAP, compare_grads, gpu_grads_as_oracle, make_ctx, oracle_view, to_dev)
 
 pytestmark = pytest.mark.gpu
 
@@ -17,13 +17,21 @@ def _build():
     oracle.build()
 
 
+def _band_mask(band):
+    """1 outside the ambiguity band, 0 inside; the band may take out at most BAND_CAP of the
+    pixels."""
+    inside = int((band != 0).sum())
+    assert inside <= BAND_CAP * band.size, (inside, band.size)
+    return (band == 0).astype(np.float64)
+
+
 def _upstream(v, band, seed):
     """Random upstream gradients, zero on ambiguity-band pixels."""
     rng = np.random.default_rng(seed)
     gD = rng.normal(size=(v.rows, v.cols))
     gN = rng.normal(size=(3, v.rows, v.cols))
     gO = rng.normal(size=(v.rows, v.cols))
-    m = (band == 0).astype(np.float64)
+    m = _band_mask(band)
     return gD * m, gN * m, gO * m
 
 
@@ -37,7 +45,7 @@ def _coherent_upstream(v, band, seed):
     gD = 1.0 + 0.2 * rng.normal(size=(v.rows, v.cols))
     gN = 0.05 * rng.normal(size=(3, v.rows, v.cols))
     gO = 0.5 + 0.1 * rng.normal(size=(v.rows, v.cols))
-    m = (band == 0).astype(np.float64)
+    m = _band_mask(band)
     return gD * m, gN * m, gO * m
 
 
