@@ -80,6 +80,8 @@ def _load():
                                                 _F, _F, _I, _P, _P, _P, _P, _P, _P]
             lib.or_contract_logf.argtypes = [_F]
             lib.or_contract_logf.restype = _F
+            lib.or_contract_reach_radius.argtypes = [_F, _F]
+            lib.or_contract_reach_radius.restype = _F
             lib.or_bin.argtypes = [_I64, _P, _P, _P, _I, _I, _I, _I, _I64, _P, _P, _I64]
             lib.or_bin.restype = _I64
             lib.or_tile_ranges.argtypes = [_I64, _P, _I64, _I64, _P, _P]
@@ -135,6 +137,11 @@ def contract_expf(x) -> float:
 
 def contract_logf(x) -> float:
     return float(_load().or_contract_logf(float(np.float32(x))))
+
+
+def contract_reach_radius(o, alpha_min=1.0 / 255.0) -> float:
+    """The binary32 contract's radius of the contributing region (splat units), with its margin."""
+    return _load().or_contract_reach_radius(float(o), float(alpha_min))
 
 
 def project_contract(pos_logit, quat, log_scale, T_ws, rows, cols, elev_min, elev_max,
@@ -628,7 +635,7 @@ def densify(views, Dt, D, O, n_d, refine=False, lambda_do=0.5, lambda_de=0.1, w0
     return pl, qt, ls, pix
 
 
-# ---- photometric registration residual (Sec. 3.4, Eq. L_photo) ---------------------------------
+# ---- photometric registration residual (Sec. 3.3.3, Eq. L_photo) ---------------------------------
 
 def _se3_right_jacobian_point(R, p):
     """d(R exp(xi^) p + t)/d xi at xi = 0 for xi = (rho, omega): R [I, -[p]x]  (3 x 6)."""
@@ -636,9 +643,10 @@ def _se3_right_jacobian_point(R, p):
     return R @ np.hstack([np.eye(3), -px])
 
 
-def photometric_normal_eqs(D, O, Dq, T_qm, rows, cols, elev_min, elev_max, o_min, huber_delta):
+def photometric_normal_eqs(D, O, Dq, T_qm, rows, cols, elev_min, elev_max, o_min, huber_delta,
+                           band_px=None, band_r=None):
     """Photometric residual of the rendered range image against a query range image of the same
-    sensor model, and its Gauss-Newton normal equations in the pose (Sec. 3.4, Eq. L_photo).
+    sensor model, and its Gauss-Newton normal equations in the pose (Sec. 3.3.3, Eq. L_photo).
     Reading: pixel u of the render with O(u) >= o_min has range d = D / O and point p = d v(u);
     p' = T_qm p (render frame -> query frame); u' = phi(p') has the continuous column
     c' = (pi - atan2(y', x')) / dgamma - 1/2 and row r' = (elev_max - atan2(z', |x'y'|)) /
@@ -646,7 +654,14 @@ def photometric_normal_eqs(D, O, Dq, T_qm, rows, cols, elev_min, elev_max, o_min
     Dq > 0); the residual is r = |p'| - Dq(u') (at T_qm = I it is d(u) - Dq(u)).  The pose is
     perturbed on the right, T_qm exp(xi^), xi = (rho, omega); J = dr/dxi.  Huber weights
     w = min(1, delta / |r|) (IRLS), cost rho_H(r).  Returns a dict: H = sum w J J^T (6 x 6),
-    g = sum w J r, cost, count, and per pixel r, w, J (P x 6), used (bool).  FP64."""
+    g = sum w J r, cost, count, and per pixel r, w, J (P x 6), used (bool).  FP64.
+
+    Ambiguity band (test infrastructure: the pixels on which a binary32 evaluation of the same
+    residual may legitimately disagree), when band_px is given: band[i] is set for a pixel with
+    O >= o_min whose u' lies within band_px of a cell edge in rows or columns (the floor of u'
+    picks the bilinear cell, the validity of its four pixels and the slopes that enter J), or
+    whose bilinear slopes move the sample by more than band_r when u' moves by band_px
+    ((|dS/dc'| + |dS/dr'|) band_px > band_r)."""
     D = np.asarray(D, np.float64).ravel()
     O = np.asarray(O, np.float64).ravel()
     Dq = np.asarray(Dq, np.float64).reshape(rows, cols)
@@ -660,6 +675,7 @@ def photometric_normal_eqs(D, O, Dq, T_qm, rows, cols, elev_min, elev_max, o_min
     wts = np.zeros(P)
     J = np.zeros((P, 6))
     used = np.zeros(P, bool)
+    band = np.zeros(P, bool)
     H = np.zeros((6, 6))
     g = np.zeros(6)
     cost = 0.0
@@ -678,10 +694,13 @@ def photometric_normal_eqs(D, O, Dq, T_qm, rows, cols, elev_min, elev_max, o_min
         cp = (math.pi - math.atan2(y, x)) / dg - 0.5
         rp = (elev_max - math.atan2(z, rxy)) / dth if rows > 1 else 0.0
         r0 = math.floor(rp)
-        if r0 < 0 or r0 + 1 >= rows:
-            continue
         c0 = math.floor(cp)
         fr, fc = rp - r0, cp - c0
+        if band_px is not None and ((rows > 1 and min(fr, 1.0 - fr) <= band_px)
+                                    or min(fc, 1.0 - fc) <= band_px):
+            band[i] = True
+        if r0 < 0 or r0 + 1 >= rows:
+            continue
         ca, cb = c0 % cols, (c0 + 1) % cols
         q00, q01, q10, q11 = Dq[r0, ca], Dq[r0, cb], Dq[r0 + 1, ca], Dq[r0 + 1, cb]
         if not (q00 > 0 and q01 > 0 and q10 > 0 and q11 > 0):
@@ -689,6 +708,8 @@ def photometric_normal_eqs(D, O, Dq, T_qm, rows, cols, elev_min, elev_max, o_min
         sample = (1 - fr) * ((1 - fc) * q00 + fc * q01) + fr * ((1 - fc) * q10 + fc * q11)
         dS_dc = (1 - fr) * (q01 - q00) + fr * (q11 - q10)
         dS_dr = (1 - fc) * (q10 - q00) + fc * (q11 - q01)
+        if band_px is not None and (abs(dS_dc) + abs(dS_dr)) * band_px > band_r:
+            band[i] = True
         dc_dq = np.array([y, -x, 0.0]) / (dg * rxy2)
         dth_dq = np.array([-z * x / (rxy * rho * rho), -z * y / (rxy * rho * rho), rxy / (rho * rho)])
         dr_dq = -dth_dq / dth
@@ -702,4 +723,4 @@ def photometric_normal_eqs(D, O, Dq, T_qm, rows, cols, elev_min, elev_max, o_min
         g += w * Ji * r
         res[i], wts[i], J[i], used[i] = r, w, Ji, True
     return {"H": H, "g": g, "cost": cost, "count": int(used.sum()), "r": res, "w": wts, "J": J,
-            "used": used}
+            "used": used, "band": band}

@@ -222,6 +222,18 @@ float or_contract_logf(float x)
  * Out: pixel rows [r0, r1], cyclic pixel columns [c0, c0 + nc) mod W, tile rows [tr0, tr1],
  * cyclic tile columns [tc0, tc0 + ntc) mod TC.  Returns the number of tiles (0 when no pixel ray
  * can reach the region). */
+/* Radius of the contributing region in splat units: o G(s) >= alpha_min holds for
+ * |s| <= sqrt(2 ln(o / alpha_min)), widened by 0.1 % + 0.002 to cover the binary32 rounding of
+ * alpha on the GPU; 0 when o < 0.999 alpha_min (nothing can contribute), and o below alpha_min
+ * by less than that is taken at alpha_min (radius 0.002). */
+float or_contract_reach_radius(float o, float alpha_min)
+{
+    float x = o / alpha_min;
+    if (x < 0.999f) return 0.0f;
+    if (x < 1.0f) x = 1.0f;
+    return sqrtf(2.0f * or_contract_logf(x)) * 1.001f + 0.002f;
+}
+
 /* keep the higher and the lower of the points seen so far, by elevation atan2(z, r), r >= 0:
  * z r' > z' r says that (z, r) lies above (z', r'); the first of equal points stays */
 static void elev_candidate(float z, float r, float *zh, float *rh, float *zl, float *rl, int *have)
@@ -239,10 +251,8 @@ static int contract_bbox(f3 ba, f3 bb, f3 bc, float o, float alpha_min, float si
                          int32_t *til)
 {
     const float eps = 0.01f; /* pixel-unit margin */
-    float x = o / alpha_min;
-    if (x < 0.999f) return 0;
-    if (x < 1.0f) x = 1.0f;
-    float ro = sqrtf(2.0f * or_contract_logf(x)) * 1.001f + 0.002f;
+    float ro = or_contract_reach_radius(o, alpha_min);
+    if (ro == 0.0f) return 0;
     float a = ro < sigma ? ro : sigma;
     float k = (1.41421356f * ro) / a;   /* diamond |u| + |v| <= k in units of a */
     f3 A = { a * ba.x, a * ba.y, a * ba.z };

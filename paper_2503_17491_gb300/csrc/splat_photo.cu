@@ -1,4 +1,4 @@
-// Photometric registration residual (Sec. 3.4, Eq. L_photo) and its Gauss-Newton normal
+// Photometric registration residual (Sec. 3.3.3, Eq. L_photo) and its Gauss-Newton normal
 // equations in the pose, reduced over one view's pixels.
 //
 // Pixel u of the rendered view with O(u) >= o_min: d = D / O, p = d v(u), p' = T p with T the

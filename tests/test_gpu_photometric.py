@@ -29,12 +29,25 @@ def _setup(n=30_000, rows=64, cols=1024):
     return s, vm, Dq, T_true
 
 
-def test_photometric_parity_on_a_rendered_view():
+# Ambiguity band of the photometric residual (oracle.photometric_normal_eqs): pixels whose u' lies
+# within PHOTO_BAND_PX of a cell edge (the binary32 floor of u' may pick the neighbouring bilinear
+# cell), or where the query image's slopes move the sample by more than PHOTO_BAND_R when u' moves
+# by PHOTO_BAND_PX.  PHOTO_BAND_PX is about the binary32 error of u' (c' near 1024 columns carries
+# a rounding of 6e-5 px, the arctangent about as much again); measured on GB300 on both scenes
+# below, no pixel differed from the oracle by more than 6.1e-4 m in r or 2.7e-4 in J even with no
+# band at all.
+PHOTO_BAND_PX, PHOTO_BAND_R = 1e-4, 1e-3
+
+
+@pytest.mark.parametrize("n,rows", [(30_000, 64), (100_000, 128)])
+def test_photometric_parity_on_a_rendered_view(n, rows):
     """The render of the map at the model pose against a ray-cast query scan: per-pixel
-    residuals, weights and Jacobians, and the reduced normal equations."""
-    s, vm, Dq, T_true = _setup()
+    residuals, weights and Jacobians within 1e-3 of the oracle's outside the ambiguity band (at
+    most 1 % of the used pixels), the same set of used pixels everywhere, and the reduced normal
+    equations of the unflagged pixels within 1e-3."""
+    s, vm, Dq, T_true = _setup(n=n, rows=rows)
     ctx = make_ctx(s.n, [vm])
-    d, n, a = ctx.render(*to_dev(s))
+    d, nn, a = ctx.render(*to_dev(s))
     T = (T_true @ se3_exp([0.05, -0.03, 0.01, 0.002, 0.0, 0.004])).astype(np.float32)
     out, px = ctx.photometric(0, d, a, torch.from_numpy(Dq).cuda(), _t34(T), o_min=0.5,
                               huber_delta=0.3, per_pixel=True)
@@ -43,17 +56,20 @@ def test_photometric_parity_on_a_rendered_view():
     T64 = np.eye(4)
     T64[:3] = T[:3].astype(np.float64)
     ref = oracle.photometric_normal_eqs(D, O, Dq.astype(np.float64), T64, vm.rows, vm.cols,
-                                        vm.elev_min, vm.elev_max, 0.5, 0.3)
+                                        vm.elev_min, vm.elev_max, 0.5, 0.3,
+                                        band_px=PHOTO_BAND_PX, band_r=PHOTO_BAND_R)
     px = px.cpu().numpy().astype(np.float64)
     used = px[1] > 0
-    agree = used == ref["used"]
-    assert ref["count"] > 5000 and agree.mean() > 0.999, agree.mean()
-    both = used & ref["used"]
-    r_ok = np.abs(px[0][both] - ref["r"][both]) <= 2e-3 + 1e-4 * np.abs(ref["r"][both])
+    assert ref["count"] > 5000
+    ok = ~ref["band"]
+    assert (ref["band"] & ref["used"]).sum() <= 0.01 * ref["count"]
+    np.testing.assert_array_equal(used[ok], ref["used"][ok])
+    both = used & ref["used"] & ok
+    assert np.abs(px[0][both] - ref["r"][both]).max() <= 1e-3
+    assert np.abs(px[1][both] - ref["w"][both]).max() <= 1e-3
     J = px[2:].T[both]
     Jr = ref["J"][both]
-    J_ok = (np.abs(J - Jr) <= 1e-3 * np.maximum(np.abs(Jr).max(1, keepdims=True), 1.0)).all(1)
-    assert r_ok.mean() > 0.999 and J_ok.mean() > 0.995, (r_ok.mean(), J_ok.mean())
+    assert (np.abs(J - Jr) <= 1e-3 * np.maximum(np.abs(Jr).max(1, keepdims=True), 1.0)).all()
     # the reduction equals the sum of the kernel's own per-pixel terms
     H, g, cost, count = api.unpack_normal_eqs(out)
     w = px[1]
@@ -62,10 +78,17 @@ def test_photometric_parity_on_a_rendered_view():
     assert count == int(used.sum())
     np.testing.assert_allclose(H, Hs, rtol=1e-4, atol=1e-4 * np.abs(Hs).max())
     np.testing.assert_allclose(g, gs, rtol=1e-4, atol=1e-4 * np.abs(gs).max())
-    # and the oracle's normal equations
-    assert np.linalg.norm(H - ref["H"]) <= 5e-3 * np.linalg.norm(ref["H"])
-    assert np.linalg.norm(g - ref["g"]) <= 2e-2 * np.linalg.norm(ref["g"])
-    assert cost == pytest.approx(ref["cost"], rel=1e-2)
+    # the normal equations of the unflagged pixels against the oracle's
+    wu = np.where(both, w, 0.0)
+    Hu = (px[2:] * wu) @ px[2:].T
+    gu = (px[2:] * wu) @ px[0]
+    Jo, wo, ro = ref["J"], np.where(both, ref["w"], 0.0), ref["r"]
+    Ho = (Jo.T * wo) @ Jo
+    go = (Jo.T * wo) @ ro
+    assert np.linalg.norm(Hu - Ho) <= 1e-3 * np.linalg.norm(Ho)
+    assert np.linalg.norm(gu - go) <= 1e-3 * np.linalg.norm(go)
+    # the Huber cost over all used pixels
+    assert cost == pytest.approx(ref["cost"], rel=1e-3)
 
 
 def test_gauss_newton_on_the_gpu_recovers_a_known_pose():

@@ -214,3 +214,160 @@ def test_bbox_is_clipped_to_the_contributing_region(oracle_mod, o, bound):
     half = math.atan(a * s / d) / dg               # columns each side of the centre
     nc = int(proj["pix_rect"][0][3])
     assert 2 * half - 1 <= nc <= 2 * half * 1.003 + 3, (nc, half)
+
+
+# ---- tightness against the exact FP64 footprint of the contributing region -------------------
+#
+# The binary32 contract bounds the part of the splat plane where a primitive can contribute
+# (Sec. 3.2.3 reading: the 3-sigma square cut by o G(s) >= alpha_min, the disk |s| <= r_o).  The
+# pins below compute that region's angular footprint independently, in FP64 from the parameters
+# (quaternion -> axes, scales, sensor frame, densely sampled region boundary, exact corners), and
+# bound the contract's pixel rectangle from both sides: it holds every pixel centre of the
+# footprint, and it exceeds the footprint by at most one pixel of rounding beyond TIGHT_FRAC of
+# the footprint's half-width.  The contract's polygon circumscribes the region with edges at most
+# 1/cos(pi/8) - 1 = 8.2 % of its radius outside it (a regular octagon around a disk is the worst
+# case), hence TIGHT_FRAC = 0.1.  Primitives whose region holds a pole ray, spans a quarter turn
+# of azimuth or lies in a plane through the sensor are left to the hand-built cases above.
+
+TIGHT_FRAC = 0.1
+
+
+def _quat_axes(q):
+    q = q / np.linalg.norm(q, axis=1, keepdims=True)
+    w, x, y, z = q.T
+    ta = np.stack([1 - 2 * (y * y + z * z), 2 * (x * y + w * z), 2 * (x * z - w * y)], 1)
+    tb = np.stack([2 * (x * y - w * z), 1 - 2 * (x * x + z * z), 2 * (y * z + w * x)], 1)
+    return ta, tb
+
+
+def _footprint(pl, q, ls, view, sigma=3.0, amin=1.0 / 255.0, K=2048):
+    """Continuous pixel extent [r_lo, r_hi] x [c_lo, c_hi] of each primitive's contributing
+    region seen from the view (FP64), and a mask of the primitives it is defined for."""
+    pl, q, ls = (np.asarray(a, np.float64) for a in (pl, q, ls))
+    Rws, tws = view.T_ws[:3, :3], view.T_ws[:3, 3]
+    Rcw, tcw = Rws.T, -Rws.T @ tws
+    ta, tb = _quat_axes(q)
+    s = np.exp(ls)
+    o = 1.0 / (1.0 + np.exp(-pl[:, 3]))
+    ba = s[:, :1] * (ta @ Rcw.T)
+    bb = s[:, 1:] * (tb @ Rcw.T)
+    bc = pl[:, :3] @ Rcw.T + tcw
+    ok = o > amin
+    ro = np.sqrt(2.0 * np.log(np.maximum(o / amin, 1.0)))
+    a = np.minimum(ro, sigma)
+    # boundary of {|s|_inf <= a} n {|s| <= ro}: K directions plus the exact corners
+    t = np.linspace(0.0, 2.0 * np.pi, K, endpoint=False)
+    U = np.stack([np.cos(t), np.sin(t)], 1)
+    out = {k: np.zeros(len(o)) for k in ("r_lo", "r_hi", "c_lo", "c_hi", "span")}
+    for i0 in range(0, len(o), 256):
+        sl = slice(i0, i0 + 256)
+        rad = np.minimum(ro[sl, None], a[sl, None] / np.abs(U).max(1)[None])
+        S = rad[..., None] * U[None]                                   # (m, K, 2)
+        h = np.sqrt(np.maximum(ro[sl] ** 2 - a[sl] ** 2, 0.0))
+        h = np.minimum(h, a[sl])
+        corners = np.stack([np.stack([sa * a[sl], sb * h], 1) for sa in (-1, 1) for sb in (-1, 1)] +
+                           [np.stack([sb * h, sa * a[sl]], 1) for sa in (-1, 1) for sb in (-1, 1)], 1)
+        S = np.concatenate([S, corners], 1)
+        X = bc[sl, None] + S[..., :1] * ba[sl, None] + S[..., 1:] * bb[sl, None]
+        gam = np.arctan2(X[..., 1], X[..., 0])
+        th = np.arctan2(X[..., 2], np.hypot(X[..., 0], X[..., 1]))
+        gc = np.arctan2(bc[sl, 1], bc[sl, 0])
+        d = (gam - gc[:, None] + np.pi) % (2.0 * np.pi) - np.pi
+        dg = 2.0 * np.pi / view.cols
+        dth = (view.elev_max - view.elev_min) / (view.rows - 1)
+        out["c_lo"][sl] = (np.pi - (gc + d.max(1))) / dg - 0.5
+        out["c_hi"][sl] = (np.pi - (gc + d.min(1))) / dg - 0.5
+        out["r_lo"][sl] = (view.elev_max - th.max(1)) / dth
+        out["r_hi"][sl] = (view.elev_max - th.min(1)) / dth
+        out["span"][sl] = d.max(1) - d.min(1)
+    # the z axis through the region (pole), a plane through the sensor
+    det = ba[:, 0] * bb[:, 1] - ba[:, 1] * bb[:, 0]
+    with np.errstate(divide="ignore", invalid="ignore"):
+        u = -(bc[:, 0] * bb[:, 1] - bc[:, 1] * bb[:, 0]) / det
+        v = -(ba[:, 0] * bc[:, 1] - ba[:, 1] * bc[:, 0]) / det
+    pole = (np.abs(u) <= a * 1.01) & (np.abs(v) <= a * 1.01) & (u * u + v * v <= (1.01 * ro) ** 2)
+    nrm = np.cross(ba, bb)
+    nrm /= np.linalg.norm(nrm, axis=1, keepdims=True)
+    through = np.abs(np.sum(nrm * bc, 1)) < 1e-3
+    out["good"] = ok & ~pole & ~through & np.isfinite(det) & (out["span"] < np.pi / 2)
+    return out
+
+
+def _rect_excess(oracle_mod, pl, q, ls, view, th=16, tw=16):
+    """Per selected primitive and edge (top, bottom, left, right): how far the contract's pixel
+    rectangle reaches beyond the exact footprint (pixels, > -1 means every pixel centre of the
+    footprint is inside), and the footprint's half-width along that axis."""
+    proj = oracle_mod.project_contract(pl, q, ls, view.T_ws, view.rows, view.cols,
+                                       view.elev_min, view.elev_max, th, tw)
+    fp = _footprint(pl, q, ls, view)
+    rect = proj["pix_rect"].astype(np.float64)
+    H, W = view.rows, view.cols
+    inside_rows = (fp["r_lo"] > 0) & (fp["r_hi"] < H - 1)    # no clipping at the image edge
+    has_px = (np.ceil(fp["r_lo"]) <= np.floor(fp["r_hi"])) & \
+             (np.ceil(fp["c_lo"]) <= np.floor(fp["c_hi"]))
+    sel = fp["good"] & inside_rows & has_px
+    assert np.all(proj["count"][sel] > 0)
+    c0 = rect[:, 2] + W * np.round((fp["c_lo"] - rect[:, 2]) / W)   # unwrap to the footprint
+    c1 = c0 + rect[:, 3] - 1
+    ex = np.stack([fp["r_lo"] - rect[:, 0], rect[:, 1] - fp["r_hi"],
+                   fp["c_lo"] - c0, c1 - fp["c_hi"]], 1)[sel]
+    hr, hc = (fp["r_hi"] - fp["r_lo"]) / 2, (fp["c_hi"] - fp["c_lo"]) / 2
+    hw = np.stack([hr, hr, hc, hc], 1)[sel]
+    return ex, hw, proj, sel
+
+
+def _tight_scenes():
+    out = []
+    for seed in range(3):
+        s = scenes.tiny_scene(400, seed, rows=64, cols=1024, fov_deg=22.5, dist=(0.5, 12.0),
+                              spread=1.5, log_scale=(-3.0, -0.5))
+        s.views[0].T_ws = scenes.random_pose(np.random.default_rng(seed + 20), 0.5, 30.0)
+        out.append(s)
+    s = scenes.workload(1, n=4000)
+    out.append(s)
+    return out
+
+
+@pytest.mark.parametrize("k", range(4))
+def test_box_is_tight_around_the_exact_footprint(oracle_mod, k):
+    """Random posed scenes (near, large splats on a 64 x 1024 image; a street): every edge of the
+    contract's rectangle lies within 1 px + TIGHT_FRAC x half-width of the exact FP64 footprint
+    of the contributing region, and no pixel centre of the footprint is outside it."""
+    s = _tight_scenes()[k]
+    v = s.views[0]
+    ex, hw, proj, sel = _rect_excess(oracle_mod, s.pos_logit, s.quat, s.log_scale, v)
+    assert sel.sum() >= 200 and (hw > 10).sum() >= 50       # large footprints are tested
+    assert ex.min() > -1.0, ex.min()                          # coverage of every pixel centre
+    worst = (ex - (1.0 + TIGHT_FRAC * hw)).max()
+    assert worst <= 0.0, (worst, ex.max())
+
+
+def test_rectangle_pixels_per_reached_pixel(oracle_mod):
+    """Summed over the random posed scenes, the contract's rectangles hold at most 1.9 pixels per
+    (pixel, primitive) pair whose ray reaches the primitive in FP64 (brute force)."""
+    rect_px = reach = 0
+    for s in _tight_scenes()[:3]:
+        v = s.views[0]
+        proj = oracle_mod.project_contract(s.pos_logit, s.quat, s.log_scale, v.T_ws, v.rows,
+                                           v.cols, v.elev_min, v.elev_max)
+        params = oracle_mod.split_params(s.pos_logit, s.quat, s.log_scale)
+        pix, prim = oracle_mod.reach_pairs(params, v.T_ws, v.rows, v.cols, v.elev_min, v.elev_max)
+        pr = proj["pix_rect"].astype(np.int64)
+        area = (pr[:, 1] - pr[:, 0] + 1) * pr[:, 3]
+        rect_px += int(np.where(proj["count"] > 0, area, 0).sum())
+        reach += len(pix)
+    assert reach > 100_000
+    assert rect_px <= 1.9 * reach, rect_px / reach
+
+
+def test_contract_reach_radius_margin(oracle_mod):
+    """The contract's radius of the contributing region is the closed form
+    sqrt(2 ln(o / alpha_min)) (o exp(-r^2 / 2) = alpha_min) widened by 0.1 % + 0.002, to binary32
+    rounding; nothing below alpha_min."""
+    amin = 1.0 / 255.0
+    for o in np.concatenate([np.linspace(0.0045, 0.99, 200), [amin * 1.0001, 0.5]]):
+        o = float(np.float32(o))
+        exact = math.sqrt(2.0 * math.log(o / float(np.float32(amin))))
+        got = oracle_mod.contract_reach_radius(o, amin)
+        assert abs(got - (exact * 1.001 + 0.002)) <= 2e-6 * max(exact, 1.0) + 1e-6, (o, got, exact)
+    assert oracle_mod.contract_reach_radius(0.5 * amin, amin) == 0.0

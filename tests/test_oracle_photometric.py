@@ -1,4 +1,4 @@
-"""Pins of the oracle's photometric registration residual (Sec. 3.4, Eq. L_photo) and its
+"""Pins of the oracle's photometric registration residual (Sec. 3.3.3, Eq. L_photo) and its
 Gauss-Newton normal equations."""
 import math
 
@@ -111,3 +111,40 @@ def test_gauss_newton_recovers_a_known_pose():
         T = T @ se3_exp(dx)
     e1 = err(T)
     assert e1[0] < 0.2 * e0[0] and e1[1] < 0.2 * e0[1], (e0, e1)
+
+
+def test_ambiguity_band_flags_cell_edges_and_steep_slopes():
+    """The band flags exactly the used pixels whose u' lies within band_px of a cell edge (u'
+    from the motion's closed form: a turn of 0.3 columns about z and a 0.2 m lift), plus, on a
+    query image ramping across columns by s metres per column, every pixel when s band_px
+    exceeds band_r and no extra pixel when it does not."""
+    rows, cols, emin, emax = 24, 256, -0.3, 0.3
+    dg, dth = 2 * math.pi / cols, (emax - emin) / (rows - 1)
+    phi = 0.3 * dg
+    T = se3_exp([0.0, 0.0, 0.2, 0.0, 0.0, phi])
+    T[:3, 3] = [0.0, 0.0, 0.2]                 # a pure lift after the turn about z
+    D = np.full(rows * cols, 10.0)
+    O = np.ones(rows * cols)
+    # u' of every pixel: p = 10 v(u), p' = Rz(phi) p + (0, 0, 0.2)
+    r, c = np.divmod(np.arange(rows * cols), cols)
+    gam = math.pi - (c + 0.5) * dg
+    th = emax - r * dth
+    x, y, z = 10 * np.cos(th) * np.cos(gam + phi), 10 * np.cos(th) * np.sin(gam + phi), 10 * np.sin(th) + 0.2
+    cq = (math.pi - np.arctan2(y, x)) / dg - 0.5
+    rq = (emax - np.arctan2(z, np.hypot(x, y))) / dth
+    fr, fc = rq - np.floor(rq), cq - np.floor(cq)
+    bp = 0.25
+    near = (np.minimum(fr, 1 - fr) <= bp) | (np.minimum(fc, 1 - fc) <= bp)
+    for s, steep in ((0.01, False), (1.0, True)):
+        Dq = 10.0 + s * np.tile(np.arange(cols, dtype=float), rows)
+        out = oracle.photometric_normal_eqs(D, O, Dq, T, rows, cols, emin, emax, 0.5, 1.0,
+                                            band_px=bp, band_r=0.005)
+        used = out["used"]
+        assert used.sum() > 0.8 * rows * cols
+        seam = (c == 0) | (c == cols - 1)      # the ramp wraps from 255 s back to 0 there
+        m = ~seam & (np.floor(rq) >= 0) & (np.floor(rq) + 1 < rows)
+        if steep:
+            assert out["band"][m].all()
+        else:
+            np.testing.assert_array_equal(out["band"][m], near[m])
+            assert 0 < near[m].sum() < m.sum()
