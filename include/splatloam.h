@@ -298,7 +298,7 @@ SPLAT_API int splat_densify(splat_ctx *ctx, const float *target_depth, const flo
                             int64_t capacity, void *stream);
 
 /* Photometric registration residual of a rendered view against a query range image of the same
- * sensor model, with its Gauss-Newton normal equations in the pose (Sec. 3.4, Eq. L_photo; the
+ * sensor model, with its Gauss-Newton normal equations in the pose (Sec. 3.3.3, Eq. L_photo; the
  * pose update T <- T exp(delta) of that section).  For pixel u of view `view` with
  * O(u) >= o_min: d = D / O, p = d v(u) (render frame), p' = T p (query frame),
  * u' = phi(p') with continuous column c' = (pi - atan2(y', x')) / dgamma - 1/2 and row
@@ -332,10 +332,6 @@ SPLAT_API int splat_loss(const float *depth, const float *normal, const float *a
                          int64_t n_pixels, const splat_loss_config *cfg, float *dL_ddepth,
                          float *dL_dnormal, float *dL_dalpha, double *loss_out, void *stream);
 
-/* One bias-corrected Adam step of n primitives in place: params (pos_logit, quat, log_scale),
- * their gradients (same layout), first and second moments m_*, v_* (same layouts, caller-owned,
- * zero before the first step) and a device int32 step counter that the call increments
- * (the update uses t = *step + 1).  Errors: INVALID_ARG, CUDA. */
 /* The loss of splat_loss over the packed images of the context's registered views (P =
  * ctx's pixel count), with either normal mode of splat_loss_config; every registered view counts
  * (keyframe sampling applies inside splat_refine_step only).  target_normal may be NULL when
@@ -347,6 +343,10 @@ SPLAT_API int splat_view_loss(splat_ctx *ctx, const float *depth, const float *n
                               float *dL_ddepth, float *dL_dnormal, float *dL_dalpha,
                               double *loss_out, void *stream);
 
+/* One bias-corrected Adam step of n primitives in place: params (pos_logit, quat, log_scale),
+ * their gradients (same layout), first and second moments m_*, v_* (same layouts, caller-owned,
+ * zero before the first step) and a device int32 step counter that the call increments
+ * (the update uses t = *step + 1).  Errors: INVALID_ARG, CUDA. */
 SPLAT_API int splat_adam_step(float *pos_logit, float *quat, float *log_scale,
                               const float *g_pos_logit, const float *g_quat,
                               const float *g_log_scale, float *m_pos_logit, float *m_quat,
@@ -374,8 +374,13 @@ SPLAT_API int splat_refine_step(splat_ctx *ctx, float *pos_logit, float *quat, f
  * device memory (for instance a process whose device memory is owned by another allocator, or
  * code that must not call cudaMalloc once it is running).  It renders one view like
  * splat_render, with no context: every workspace buffer lives in one array of the library
- * (about 8 MB, held on every device that loads the library until the process exits), and the
- * call allocates nothing -- no cudaMalloc, cudaFree or host heap.
+ * (about 8 MB), and the call allocates nothing -- no cudaMalloc, cudaFree or host heap.
+ * The array and the kernels' code take device memory when CUDA loads the library's code on a
+ * device, and keep it until the process exits.  CUDA loads that code when it is first used on
+ * the device (lazy module loading is CUDA's default), so the FIRST call on each device is a
+ * set-up call: it loads the code it uses and looks up the array's device address, with that
+ * device current.  Make that first call before handing the device's memory to another
+ * allocator, and outside any stream capture; every later call allocates nothing.
  * Limits: g->n <= 16384 primitives, rows <= 256, rows * cols <= 65536 pixels, at most 4096
  * tiles and 262144 (tile, primitive) pairs.  cfg = NULL uses splat_default_config.
  * Outputs: depth[P], normal[3][P], alpha[P] (P = rows * cols), as splat_render.
@@ -383,8 +388,7 @@ SPLAT_API int splat_refine_step(splat_ctx *ctx, float *pos_logit, float *quat, f
  * beyond the limits, bad pose or intrinsics), UNSUPPORTED (tile shape), CAPACITY (more pairs
  * than the limit: outputs invalid), NONFINITE (a primitive had a non-finite value: it was
  * skipped), CUDA.  All calls share the one array, which keeps the previous call's contents:
- * calls that overlap on the GPU, or come from several host threads at once, race.  The first
- * call on each device looks up the array's device address, with that device current. */
+ * calls that overlap on the GPU, or come from several host threads at once, race. */
 SPLAT_API int splat_render_noalloc(const splat_gaussians *g, const double T_world_sensor[16],
                                    const splat_lidar_intrinsics *intr,
                                    const splat_render_config *cfg, float *depth, float *normal,
