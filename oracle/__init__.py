@@ -118,6 +118,12 @@ def _c(a, dtype):
 # t_min, sigma_cut.
 DEFAULT_CFG = (1.0 / 255.0, 0.99, 1e-4, 3.0)
 
+# Ambiguity band of the parity checks (render(..., band=)): a pixel is flagged when one of its
+# composite decisions lies this close to its threshold -- box edge (relative to sigma),
+# alpha_min (absolute), stop on t_min (relative), in-front sign (relative to the range),
+# alpha_max clamp (absolute) -- a few times the binary32 error of each decision quantity.
+AMBIGUITY_BAND = (1e-5, 1e-6, 5e-5, 5e-7, 1e-6)
+
 
 def pose_inverse(T_ws):
     R = np.zeros(9)

@@ -477,7 +477,13 @@ class Refiner:
     one sort, persistent compositing over the tiles of all keyframes, loss, backward, fused
     Adam), captured once in a CUDA graph and replayed.
     mode="plain": one launch sequence per keyframe (render, loss, backward with accumulation),
-    then one Adam step -- no graph.
+    then one Adam step -- no graph; every keyframe has its own context, registered once, so a
+    step is launches only.
+    mode="plain_reregister": the same launch sequences on one shared context that registers each
+    keyframe before rendering it (what a caller of the one-view splat_render does: the view
+    tables are rebuilt on the host and uploaded synchronously for every keyframe of every step).
+    max_pairs is the pair capacity of the batched context, or of each plain context (default:
+    generous for the views it renders).
     """
 
     def __init__(self, params, views, targets, mode="batched", cfg: RenderConfig | None = None,
@@ -498,9 +504,22 @@ class Refiner:
             self.t_depth = torch.cat([t[0].reshape(-1) for t in targets]).contiguous()
             self.t_normal = torch.cat([t[1].reshape(3, -1) for t in targets], 1).contiguous()
             self.loss_out = torch.zeros(1, dtype=torch.float64, device=dev)
-        else:
+        elif mode == "plain":
+            self.ctxs = []
+            for v in self.views:
+                c = SplatContext(self.n, 1, v.rows * v.cols,
+                                 max_pairs or default_capacity_pairs(self.n, [v]), cfg)
+                c.set_views([v])
+                self.ctxs.append(c)
+            self.ctx = self.ctxs[0]
+        elif mode == "plain_reregister":
             maxp = max(v.rows * v.cols for v in self.views)
-            self.ctx = SplatContext(self.n, 1, maxp, max_pairs, cfg)
+            big = max(self.views, key=lambda v: v.rows * v.cols)
+            self.ctx = SplatContext(self.n, 1, maxp,
+                                    max_pairs or default_capacity_pairs(self.n, [big]), cfg)
+        else:
+            raise ValueError(f"unknown mode {mode!r}")
+        if mode != "batched":
             self.targets = [(t[0].reshape(-1).contiguous(), t[1].reshape(3, -1).contiguous())
                             for t in targets]
             self.grads = tuple(torch.zeros_like(p) for p in params)
@@ -514,11 +533,15 @@ class Refiner:
     def _plain_step(self):
         self.loss_out.zero_()
         for k, v in enumerate(self.views):
-            self.ctx.set_views([v])
-            d, nrm, a = self.ctx.render(*self.params)
+            if self.mode == "plain":
+                ctx = self.ctxs[k]
+            else:
+                ctx = self.ctx
+                ctx.set_views([v])
+            d, nrm, a = ctx.render(*self.params)
             L, gD, gN, gO = loss(d, nrm, a, self.targets[k][0], self.targets[k][1], self.loss_cfg)
             self.loss_out += L
-            self.ctx.backward(*self.params, gD, gN, gO, out=self.grads, accumulate=k > 0)
+            ctx.backward(*self.params, gD, gN, gO, out=self.grads, accumulate=k > 0)
         adam_step(self.params, self.grads, self.state, self.adam_cfg)
 
     def capture(self, warmup=2):
@@ -544,6 +567,11 @@ class Refiner:
         else:
             self._plain_step()
         return self.loss_out
+
+    def close(self):
+        """Free the contexts' device workspace."""
+        for c in getattr(self, "ctxs", None) or [self.ctx]:
+            c.close()
 
     def save(self, path):
         """Checkpoint the map and the optimiser state (save_checkpoint)."""
@@ -661,10 +689,12 @@ class Mapper:
         self.n += self.n_new
         return self.n
 
-    def refine(self, iters: int) -> list[float]:
+    def refine(self, iters: int, read_losses: bool = True) -> list[float]:
         """Refinement iterations over the registered keyframes, each on the keyframes drawn for
-        it (a fresh random stream per call); returns each iteration's loss.  Sampling is off
-        outside this call, so renders cover every keyframe."""
+        it (a fresh random stream per call); returns each iteration's loss (read_losses=False:
+        nothing is read back and the list is empty -- no host synchronisation; the last loss
+        stays in loss_out).  Sampling is off outside this call, so renders cover every
+        keyframe."""
         m_pl, m_q, m_ls, v_pl, v_q, v_ls, step = self.state
         self._refines = getattr(self, "_refines", 0) + 1
         if self.draws > 0 and len(self.views) > 1:
@@ -677,7 +707,8 @@ class Mapper:
                                      (*self._rows((m_pl, m_q, m_ls, v_pl, v_q, v_ls)), step),
                                      self.t_depth, self.t_normal, self.loss_cfg, self.adam_cfg,
                                      self.loss_out)
-                losses.append(float(self.loss_out.item()))
+                if read_losses:
+                    losses.append(float(self.loss_out.item()))
         finally:
             self.ctx.set_view_sampling(0)
         return losses

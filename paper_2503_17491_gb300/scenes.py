@@ -46,6 +46,10 @@ class Rect:
     def area(self):
         return 4.0 * self.hu * self.hv
 
+    def bound(self):
+        """Centre and radius of a sphere holding the surface."""
+        return self.c, math.hypot(self.hu, self.hv)
+
     def sample(self, k, rng):
         a = rng.uniform(-self.hu, self.hu, k)[:, None]
         b = rng.uniform(-self.hv, self.hv, k)[:, None]
@@ -76,6 +80,10 @@ class Cylinder:
 
     def area(self):
         return 2.0 * math.pi * self.r * (self.z1 - self.z0)
+
+    def bound(self):
+        return (np.array([self.cx, self.cy, 0.5 * (self.z0 + self.z1)]),
+                math.hypot(self.r, 0.5 * (self.z1 - self.z0)))
 
     def sample(self, k, rng):
         a = rng.uniform(0, 2 * math.pi, k)
@@ -112,6 +120,9 @@ class Ellipsoid:
         a, b, c = self.radii
         p = 1.6075
         return 4 * math.pi * (((a * b) ** p + (a * c) ** p + (b * c) ** p) / 3) ** (1 / p)
+
+    def bound(self):
+        return self.c, float(np.max(self.radii))
 
     def sample(self, k, rng):
         x = rng.normal(size=(k, 3))
@@ -299,11 +310,17 @@ def render_targets(scene: Scene, view: View, rng=None, noise=0.01, max_range=100
     d_w = d_s @ R.T
     best = np.full(len(d_w), np.inf)
     nrm = np.zeros((len(d_w), 3))
+    # surfaces wholly beyond max_range cannot give a valid hit: left out
+    near = []
+    for surf in scene.surfaces:
+        c, r = surf.bound()
+        if np.linalg.norm(np.asarray(c, np.float64) - o) - r <= max_range:
+            near.append(surf)
     for s0 in range(0, len(d_w), chunk):
         dw = d_w[s0:s0 + chunk]
         bt = best[s0:s0 + chunk]
         bn = nrm[s0:s0 + chunk]
-        for surf in scene.surfaces:
+        for surf in near:
             t, n = surf.intersect(o, dw)
             m = t < bt
             bt[m] = t[m]

@@ -27,7 +27,7 @@ from paper_2503_17491_gb300 import api
 # 139,264 sampled pixels of the full-size scenes (the 100k street view whole, the 1M block, the
 # 12-keyframe batch in two tile shapes, the 3M map) no pixel differed from the oracle beyond the
 # tolerances even with no band at all.
-BAND = (1e-5, 1e-6, 5e-5, 5e-7, 1e-6)
+BAND = oracle.AMBIGUITY_BAND
 BAND_CAP = 0.01   # largest fraction of compared pixels the band may take out
 
 D_TOL, COS_TOL, O_TOL, G_TOL = 1e-3, 1e-5, 1e-5, 1e-3

@@ -22,7 +22,7 @@ def test_one_rank_matches_plain_refinement():
     shard = sharded.ShardedRefiner(pb, views, tt)
     assert shard.world == 1 and shard.split == [[0, 1, 2, 3]]
     la = [float(plain.step()) for _ in range(3)]
-    lb = [shard.step() for _ in range(3)]
+    lb = [float(shard.step()) for _ in range(3)]
     torch.cuda.synchronize()
     assert lb == pytest.approx(la, rel=1e-4)
     for a, b in zip(pa, pb):
