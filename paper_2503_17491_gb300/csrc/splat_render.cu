@@ -26,10 +26,11 @@
 // frame Q = (e1, e2, e3) -- e1 the ray through the tile centre, e2 and e3 its two planes -- and
 // a primitive is staged as Q b, with the centre Q b_c kept as a float pair; Q R^c_w, Q t^c_w and
 // the pixel planes in that frame come from tables computed in FP64 on the host (float pairs).
-// h_x.b_c and h_y.b_c are formed in float-pair arithmetic (two-product / two-sum), so grazing
-// rays at range keep their accuracy.  (A cheaper binary32 pre-test that skipped this for clear
-// misses paid off only while all lanes of a warp evaluated one primitive: with 32 different pairs
-// per warp some lane always passes it.)
+// In h_x.b_c and h_y.b_c two products cancel; each pair is summed exactly inside one fused
+// multiply-add with the rounding error of the other product and the operands' low parts added
+// back (dot_pair), so grazing rays at range keep their accuracy.  (A cheaper binary32 pre-test
+// that skipped this for clear misses paid off only while all lanes of a warp evaluated one
+// primitive: with 32 different pairs per warp some lane always passes it.)
 //
 // The range is d = nu . v (nu lies on the ray, so this equals |nu| without a square root) and
 // a hit counts only when d > 0 (in front of the sensor).  Cutoffs: alpha clamped at alpha_max,
@@ -62,21 +63,24 @@ constexpr int kBlocksPerTile = kBlock / 32;
 constexpr int kAcc = 13;             // per staged primitive: g_ba'(3) g_bb'(3) g_c'(3) g_n(3) g_o
 constexpr uint32_t kFull = 0xFFFFFFFFu;
 
-// A staged primitive, as four float4 rows (structure of arrays, so that lanes reading different
-// primitives spread over the banks):
+// A staged primitive, as four float4 rows and one float (structure of arrays, so that lanes
+// reading different primitives spread over the banks):
 //   a: b_alpha' (tile frame), o        b: b_beta' (tile frame), packed pixel rectangle (bits)
 //   c: c' = Q b_c, hi part (tile frame); w: low part of c'_x
-//   n: normal (sensor frame); w: low part of c'_y
+//   n: normal (sensor frame); w: low part of c'_y            czl: low part of c'_z
 struct SlotRef {
     const float4 &a, &b, &c, &n;
+    const float &czl;
 };
 
+// a pixel's planes and ray in the tile frame; the low parts kept are those of the components
+// that enter the exact pair of each plane (h_x: 0 and 1, h_y: 0 and 2)
 struct Pix {
     float hx0, hx1, hx2;
     float hy0, hy1, hy2;
     float v0, v1, v2;
-    float hxl0, hxl1, hxl2;
-    float hyl0, hyl1, hyl2;
+    float hxl0, hxl1;
+    float hyl0, hyl2;
 };
 
 __device__ __forceinline__ float dot3e(float a0, float a1, float a2, float b0, float b1, float b2)
@@ -84,25 +88,26 @@ __device__ __forceinline__ float dot3e(float a0, float a1, float a2, float b0, f
     return __fmaf_rn(a0, b0, __fmaf_rn(a1, b1, __fmul_rn(a2, b2)));
 }
 
-// h . c with h and c as float pairs, rounded once at the end.  In the tile frame the first two
-// products are the large ones (range x pixel offset, and the centre's lateral offset) and they
-// cancel, so they are formed exactly (two-product) and summed exactly (two-sum) with their
-// low-order cross terms; the third product (sin theta0 sin dgamma times the vertical offset) is
-// small and taken in binary32.
-__device__ __forceinline__ float dot3_f2(float h0, float h1, float h2, float l0, float l1,
-                                         const float4 &c, float cl0, float cl1)
+// h . c' with h and c' as float pairs, the plane h of a pixel and c' the splat centre, both in
+// the tile frame.  Two of the three products are large (range x the pixel's angular offset from
+// the tile centre, and the centre's lateral offset from the tile's plane) and cancel to the
+// centre's offset from the pixel's plane, centimetres out of up to 100 m: for h_x they are
+// products 0 and 1, for h_y products 0 and 2.  The pair is summed inside one fused multiply-add,
+// fma(h_a, c_a, fl(h_b c_b)), which forms h_a c_a exactly and rounds only the small sum; the
+// rounding error of fl(h_b c_b) (one more fma), the low parts of both operands of the pair and
+// the third, small product are added in binary32.
+__device__ __forceinline__ float dot_pair(float ha, float ca, float hb, float cb, float hal,
+                                          float cal, float hbl, float cbl, float hc, float cc)
 {
-    const float p0 = __fmul_rn(h0, c.x), e0 = __fmaf_rn(h0, c.x, -p0);
-    const float p1 = __fmul_rn(h1, c.y), e1 = __fmaf_rn(h1, c.y, -p1);
-    float s, t;
-    two_sum(p0, p1, s, t);
-    float err = __fadd_rn(__fadd_rn(e0, e1), t);
-    err = __fmaf_rn(h0, cl0, err);
-    err = __fmaf_rn(h1, cl1, err);
-    err = __fmaf_rn(l0, c.x, err);
-    err = __fmaf_rn(l1, c.y, err);
-    err = __fmaf_rn(h2, c.z, err);
-    return __fadd_rn(s, err);
+    const float pb = __fmul_rn(hb, cb);
+    const float eb = __fmaf_rn(hb, cb, -pb);
+    const float sum = __fmaf_rn(ha, ca, pb);
+    float err = __fmaf_rn(ha, cal, eb);
+    err = __fmaf_rn(hb, cbl, err);
+    err = __fmaf_rn(hal, ca, err);
+    err = __fmaf_rn(hbl, cb, err);
+    err = __fmaf_rn(hc, cc, err);
+    return __fadd_rn(sum, err);
 }
 
 __device__ __forceinline__ Pix load_pix(const PixFrame *table, int index)
@@ -113,8 +118,8 @@ __device__ __forceinline__ Pix load_pix(const PixFrame *table, int index)
     p.hx0 = a.x; p.hx1 = a.y; p.hx2 = a.z;
     p.hy0 = a.w; p.hy1 = b.x; p.hy2 = b.y;
     p.v0 = b.z; p.v1 = b.w; p.v2 = c.x;
-    p.hxl0 = c.y; p.hxl1 = c.z; p.hxl2 = c.w;
-    p.hyl0 = d.x; p.hyl1 = d.y; p.hyl2 = d.z;
+    p.hxl0 = c.y; p.hxl1 = c.z;
+    p.hyl0 = d.x; p.hyl2 = d.z;
     return p;
 }
 
@@ -160,6 +165,7 @@ __device__ __forceinline__ int warp_incl_scan(int v, int lane)
 // block and wait to be staged (appended in walk order 32 at a time).
 struct WarpBatch {
     float4 a[32], b[32], c[32], n[32];
+    float czl[32];        // low part of c'_z
     uint32_t pos[32];     // list position of the staged entry (backward: bit 31 = flipped)
     uint32_t prim[32];    // primitive index
     float4 p0[32], p1[32], p2[32];
@@ -194,7 +200,7 @@ struct WarpQueue {
 
 __device__ __forceinline__ SlotRef slot_at(const WarpBatch &w, int s)
 {
-    return SlotRef{w.a[s], w.b[s], w.c[s], w.n[s]};
+    return SlotRef{w.a[s], w.b[s], w.c[s], w.n[s], w.czl[s]};
 }
 
 __device__ __forceinline__ void put_pix(WarpBatch &w, int lane, const Pix &p)
@@ -202,7 +208,7 @@ __device__ __forceinline__ void put_pix(WarpBatch &w, int lane, const Pix &p)
     w.p0[lane] = make_float4(p.hx0, p.hx1, p.hx2, p.hy0);
     w.p1[lane] = make_float4(p.hy1, p.hy2, p.v0, p.v1);
     w.p2[lane] = make_float4(p.v2, p.hxl0, p.hxl1, p.hyl0);
-    w.p3[lane] = p.hyl1;
+    w.p3[lane] = p.hyl2;
 }
 
 __device__ __forceinline__ Pix get_pix(const WarpBatch &w, int l)
@@ -213,8 +219,8 @@ __device__ __forceinline__ Pix get_pix(const WarpBatch &w, int l)
     p.hx0 = a.x; p.hx1 = a.y; p.hx2 = a.z;
     p.hy0 = a.w; p.hy1 = b.x; p.hy2 = b.y;
     p.v0 = b.z; p.v1 = b.w; p.v2 = c.x;
-    p.hxl0 = c.y; p.hxl1 = c.z; p.hxl2 = 0.0f;
-    p.hyl0 = c.w; p.hyl1 = d; p.hyl2 = 0.0f;
+    p.hxl0 = c.y; p.hxl1 = c.z;
+    p.hyl0 = c.w; p.hyl2 = d;
     return p;
 }
 
@@ -256,6 +262,7 @@ __device__ __forceinline__ uint32_t stage(const RenderArgs &A, const TileInfo &t
     w.n[s] = make_float4(fs * (R[0] * tn0 + R[1] * tn1 + R[2] * tn2),
                          fs * (R[3] * tn0 + R[4] * tn1 + R[5] * tn2),
                          fs * (R[6] * tn0 + R[7] * tn1 + R[8] * tn2), c[1].l);
+    w.czl[s] = c[2].l;
     return static_cast<uint32_t>(i);
 }
 
@@ -273,9 +280,9 @@ __device__ __forceinline__ bool evaluate(const SlotRef &s, const Pix &px, float 
     h.ha1 = dot3e(px.hx0, px.hx1, px.hx2, s.b.x, s.b.y, s.b.z);
     h.hb0 = dot3e(px.hy0, px.hy1, px.hy2, s.a.x, s.a.y, s.a.z);
     h.hb1 = dot3e(px.hy0, px.hy1, px.hy2, s.b.x, s.b.y, s.b.z);
-    // lateral offsets of the centre from the two pixel planes, in float-pair arithmetic
-    h.ha2 = dot3_f2(px.hx0, px.hx1, px.hx2, px.hxl0, px.hxl1, s.c, s.c.w, s.n.w);
-    h.hb2 = dot3_f2(px.hy0, px.hy1, px.hy2, px.hyl0, px.hyl1, s.c, s.c.w, s.n.w);
+    // offsets of the centre from the two pixel planes, the cancelling pair summed exactly
+    h.ha2 = dot_pair(px.hx0, s.c.x, px.hx1, s.c.y, px.hxl0, s.c.w, px.hxl1, s.n.w, px.hx2, s.c.z);
+    h.hb2 = dot_pair(px.hy0, s.c.x, px.hy2, s.c.z, px.hyl0, s.c.w, px.hyl2, s.czl, px.hy1, s.c.y);
     h.pz = __fmaf_rn(h.ha0, h.hb1, -__fmul_rn(h.ha1, h.hb0));
     h.px = __fmaf_rn(h.ha1, h.hb2, -__fmul_rn(h.ha2, h.hb1));
     h.py = __fmaf_rn(h.ha2, h.hb0, -__fmul_rn(h.ha0, h.hb2));
