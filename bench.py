@@ -646,7 +646,7 @@ def run_mapping(args):
     st = m.ctx.stats()
     # roofline of the dominant compositing kernel at the final map size (profiled extra steps)
     m.ctx.set_profiling(True)
-    fwd, bwd, fev, bev = [], [], [], []
+    fwd, bwd, fev, bev, stage_ms = [], [], [], [], []
     for _ in range(4):
         m.refine(1, read_losses=False)
         f, b = m.ctx.kernel_times()
@@ -655,7 +655,13 @@ def run_mapping(args):
         bwd.append(b)
         fev.append(s2["fwd_evals"])
         bev.append(s2["bwd_evals"])
+        stage_ms.append(m.ctx.stage_times())
     m.ctx.set_profiling(False)
+    stages = {"unit": "ms per refinement iteration at the final map (library events)",
+              "render_fwd": statistics.mean(fwd[1:]), "render_bwd": statistics.mean(bwd[1:]),
+              **{k: statistics.mean(x[k] for x in stage_ms[1:] if x.get(k) is not None)
+                 for k in stage_ms[-1] if stage_ms[-1].get(k) is not None},
+              "pairs": s2["n_pairs"], "touching": s2["n_touching"]}
     kern = {"render_fwd": (statistics.mean(fwd[1:]), statistics.mean(fev[1:])),
             "render_bwd": (statistics.mean(bwd[1:]), statistics.mean(bev[1:]))}
     dom = max(kern, key=lambda k: kern[k][0])
@@ -711,6 +717,7 @@ def run_mapping(args):
                          "note": f"the full 300-scan run's time as {S} x the sum over the timed "
                                  f"scans (each stands for {S} scans at its map size)"},
         "per_scan_ms": {"first": ms[0], "mid": ms[len(ms) // 2], "last": ms[-1]},
+        "stages": stages,
         "roofline": roofline,
         "cpu_baseline": cpu,
         "accuracy": cpu.get("accuracy") if cpu else None,
