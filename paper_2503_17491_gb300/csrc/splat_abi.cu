@@ -403,10 +403,12 @@ SPLAT_API int splat_ctx_create(const splat_render_config *cfg, const splat_capac
     if (e == cudaSuccess) e = dalloc(&c->d_trect, mpv);
     if (e == cudaSuccess) e = dalloc(&c->d_srect, mpv);
     if (e == cudaSuccess) e = dalloc(&c->d_prect, mpv);
-    if (e == cudaSuccess) e = dalloc(&c->d_tkeys, M);
-    if (e == cudaSuccess) e = dalloc(&c->d_tvals, M);
-    if (e == cudaSuccess) e = dalloc(&c->d_tkeys2, M);
-    if (e == cudaSuccess) e = dalloc(&c->d_tvals2, M);
+    // the tile-sort buffers also hold the sorted lists the forward reads four entries at a
+    // time from a 4-aligned index: 128 spare entries keep the last vector in bounds
+    if (e == cudaSuccess) e = dalloc(&c->d_tkeys, M + 128);
+    if (e == cudaSuccess) e = dalloc(&c->d_tvals, M + 128);
+    if (e == cudaSuccess) e = dalloc(&c->d_tkeys2, M + 128);
+    if (e == cudaSuccess) e = dalloc(&c->d_tvals2, M + 128);
     if (e == cudaSuccess) e = dalloc(&c->d_block_sums, splat::kScanGrid);
     if (e == cudaSuccess) e = dalloc(&c->d_hist, static_cast<size_t>(splat::kHistWords));
     if (e == cudaSuccess) e = dalloc(&c->d_ranges, TT);

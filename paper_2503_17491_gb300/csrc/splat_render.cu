@@ -192,10 +192,13 @@ __device__ __forceinline__ void list_candidates(uint16_t *cand, uint32_t m, int 
     for (; j < first + span; ++j) cand[j] = static_cast<uint16_t>(lane << 5);
 }
 
+// entries of the tile's list that meet the warp's block, waiting to be staged: fewer than 32
+// left over from the last chunk plus up to 128 from the next
+constexpr int kQueue = 160;
 struct WarpQueue {
-    uint32_t p[64];      // pair id
-    uint32_t rect[64];   // pixel rectangle inside the tile
-    uint32_t pos[64];    // list position, bit 31: normal flipped
+    uint32_t p[kQueue];      // pair id
+    uint32_t rect[kQueue];   // pixel rectangle inside the tile
+    uint32_t pos[kQueue];    // list position, bit 31: normal flipped
 };
 
 __device__ __forceinline__ SlotRef slot_at(const WarpBatch &w, int s)
@@ -353,19 +356,6 @@ __device__ __forceinline__ BlockPix block_pixel(const TileInfo &ti, int blk, int
     return b;
 }
 
-// read one list entry per lane if it meets the warp's block blk: pair id, rectangle inside the
-// tile, normal flip
-__device__ __forceinline__ bool read_entry(const RenderArgs &A, uint32_t j, int blk, uint32_t &p,
-                                           uint32_t &rect, bool &flip)
-{
-    if (!((A.entry_blocks[j] >> blk) & 1u)) return false;
-    p = A.sorted_vals[j];
-    const uint32_t r = A.entry_rect[j];
-    flip = (r & kRectFlip) != 0u;
-    rect = r & ~kRectFlip;
-    return true;
-}
-
 // Candidate numbering of a staged batch: lane b holds its primitive's live-pixel mask m, the
 // count before it (off) and, after the call, the batch total K (uniform).
 struct Numbering {
@@ -455,7 +445,6 @@ __global__ void __launch_bounds__(kBlock, 3) k_render_fwd(const RenderArgs A)
     extern __shared__ __align__(16) unsigned char s_raw[];
     FwdShared &sh = *reinterpret_cast<FwdShared *>(s_raw);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const uint32_t lt_mask = (1u << lane) - 1u;
     WarpBatch &w = sh.w[warp];
     TileInfo &ti = sh.ti[warp];
     WarpQueue &q = sh.q[warp];
@@ -477,14 +466,15 @@ __global__ void __launch_bounds__(kBlock, 3) k_render_fwd(const RenderArgs A)
         uint32_t chain = kNoChunk;   // this item's last record chunk
         int fill = 0;                 // records in it
 
-        // stage queue entries [0, cnt) and composite them, round by round
-        auto composite = [&](int cnt) {
+        // stage queue entries [off, off + cnt) and composite them, round by round
+        auto composite = [&](int cnt, int off) {
             uint32_t m = 0u;
             w.hits[lane] = 0u;
+            const int qi = off + lane;
             if (lane < cnt) {
-                stage(A, ti, q.p[lane], (q.pos[lane] >> 31) != 0, q.rect[lane], w, lane);
-                w.pos[lane] = q.pos[lane] & 0x7FFFFFFFu;
-                m = pixel_mask(q.rect[lane], bp.br, bp.bc);
+                stage(A, ti, q.p[qi], (q.pos[qi] >> 31) != 0, q.rect[qi], w, lane);
+                w.pos[lane] = q.pos[qi] & 0x7FFFFFFFu;
+                m = pixel_mask(q.rect[qi], bp.br, bp.bc);
             }
             m &= __ballot_sync(kFull, !done);
             const Numbering nb = number_candidates(m, lane);
@@ -537,39 +527,79 @@ __global__ void __launch_bounds__(kBlock, 3) k_render_fwd(const RenderArgs A)
             // order, for the backward
             if (A.rec) {
                 const uint32_t hm = lane < cnt ? w.hits[lane] : 0u;
-                const uint2 r = make_uint2(q.p[lane] | (q.pos[lane] & 0x80000000u), hm);
+                const uint2 r = lane < cnt ? make_uint2(q.p[qi] | (q.pos[qi] & 0x80000000u), hm)
+                                           : make_uint2(0u, 0u);
                 append_records(A, hm != 0u, r, lane, chain, fill);
             }
         };
 
+        // Walk the tile's list 128 entries at a time from the 4-aligned entry at or below its
+        // start: each lane reads the block masks of four consecutive entries as one word (the
+        // next chunk's word is loaded ahead), the entries that meet the block are appended to
+        // the queue in list order (a warp prefix sum of the lanes' counts), with their pair ids
+        // and rectangles read as one 16-byte vector each, and every 32 queued entries are
+        // staged and composited.
+        const uint32_t *mask_words = reinterpret_cast<const uint32_t *>(A.entry_blocks);
+        const uint32_t base = rg.x & ~3u;
+        uint32_t mw = 0u;
+        if (base + 4u * lane < rg.y) mw = mask_words[(base >> 2) + lane];
         int qn = 0;
-        for (uint32_t ch = rg.x; ch < rg.y; ch += 32) {
+        for (uint32_t ch = base; ch < rg.y; ch += 128) {
             if (__all_sync(kFull, done)) break;
-            const uint32_t j = ch + lane;
-            bool rel = false, flip = false;
-            uint32_t p = 0, rect = 0;
-            if (j < rg.y) rel = read_entry(A, j, blk, p, rect, flip);
-            const uint32_t m = __ballot_sync(kFull, rel);
-            if (rel) {
-                const int pos = qn + __popc(m & lt_mask);
-                q.p[pos] = p;
-                q.rect[pos] = rect;
-                q.pos[pos] = (j - rg.x) | (flip ? 0x80000000u : 0u);
+            const uint32_t j0 = ch + 4u * lane;
+            uint32_t mnext = 0u;
+            if (j0 + 128u < rg.y) mnext = mask_words[(j0 + 128u) >> 2];
+            uint32_t rel4 = 0u;
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const uint32_t j = j0 + k;
+                if (j >= rg.x && j < rg.y && ((mw >> (8 * k + blk)) & 1u)) rel4 |= 1u << k;
             }
-            qn += __popc(m);
-            __syncwarp();
-            if (qn >= 32) {
-                composite(32);
-                if (lane < qn - 32) {
-                    q.p[lane] = q.p[32 + lane];
-                    q.rect[lane] = q.rect[32 + lane];
-                    q.pos[lane] = q.pos[32 + lane];
+            const int c4 = __popc(rel4);
+            const int incl = warp_incl_scan(c4, lane);
+            if (rel4) {
+                const uint4 pv = *reinterpret_cast<const uint4 *>(A.sorted_vals + j0);
+                const uint4 rv = *reinterpret_cast<const uint4 *>(A.entry_rect + j0);
+                const uint32_t pa[4] = {pv.x, pv.y, pv.z, pv.w};
+                const uint32_t ra[4] = {rv.x, rv.y, rv.z, rv.w};
+                int at = qn + incl - c4;
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    if ((rel4 >> k) & 1u) {
+                        q.p[at] = pa[k];
+                        q.rect[at] = ra[k] & ~kRectFlip;
+                        q.pos[at] = (j0 + k - rg.x) | ((ra[k] & kRectFlip) ? 0x80000000u : 0u);
+                        ++at;
+                    }
                 }
-                qn -= 32;
+            }
+            qn += __shfl_sync(kFull, incl, 31);
+            mw = mnext;
+            __syncwarp();
+            int head = 0;
+            while (qn - head >= 32 && !__all_sync(kFull, done)) {
+                composite(32, head);
+                head += 32;
+            }
+            if (head > 0) {   // move the rest (fewer than 32 unless all pixels are done) down
+                qn -= head;
+                if (qn >= 32) qn = 0;   // every pixel is done: the walk ends at the loop's top
+                uint32_t pp = 0u, rr = 0u, ps = 0u;
+                if (lane < qn) {
+                    pp = q.p[head + lane];
+                    rr = q.rect[head + lane];
+                    ps = q.pos[head + lane];
+                }
+                __syncwarp();
+                if (lane < qn) {
+                    q.p[lane] = pp;
+                    q.rect[lane] = rr;
+                    q.pos[lane] = ps;
+                }
                 __syncwarp();
             }
         }
-        if (qn > 0 && !__all_sync(kFull, done)) composite(qn);
+        if (qn > 0 && !__all_sync(kFull, done)) composite(qn, 0);
         if (A.rec && lane == 0) {   // an item whose records overflowed the pool keeps none
             A.rec_head[item] = fill < 0 ? kNoChunk : chain;
             A.rec_fill[item] = fill < 0 ? 0u : static_cast<uint32_t>(fill);
