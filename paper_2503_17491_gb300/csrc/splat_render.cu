@@ -555,13 +555,25 @@ __global__ void __launch_bounds__(kBlock, 3) k_render_fwd(const RenderArgs A)
                 const uint32_t j = j0 + k;
                 if (j >= rg.x && j < rg.y && ((mw >> (8 * k + blk)) & 1u)) rel4 |= 1u << k;
             }
+            uint4 pv = make_uint4(0u, 0u, 0u, 0u), rv = pv;
+            if (rel4) {
+                pv = *reinterpret_cast<const uint4 *>(A.sorted_vals + j0);
+                rv = *reinterpret_cast<const uint4 *>(A.entry_rect + j0);
+            }
+            const uint32_t pa[4] = {pv.x, pv.y, pv.z, pv.w};
+            const uint32_t ra[4] = {rv.x, rv.y, rv.z, rv.w};
+            // once some pixels of the block are saturated, an entry whose rectangle covers only
+            // saturated ones is passed over
+            const uint32_t live = __ballot_sync(kFull, !done);
+            if (live != kFull) {
+#pragma unroll
+                for (int k = 0; k < 4; ++k)
+                    if (((rel4 >> k) & 1u) && !(pixel_mask(ra[k] & ~kRectFlip, bp.br, bp.bc) & live))
+                        rel4 &= ~(1u << k);
+            }
             const int c4 = __popc(rel4);
             const int incl = warp_incl_scan(c4, lane);
             if (rel4) {
-                const uint4 pv = *reinterpret_cast<const uint4 *>(A.sorted_vals + j0);
-                const uint4 rv = *reinterpret_cast<const uint4 *>(A.entry_rect + j0);
-                const uint32_t pa[4] = {pv.x, pv.y, pv.z, pv.w};
-                const uint32_t ra[4] = {rv.x, rv.y, rv.z, rv.w};
                 int at = qn + incl - c4;
 #pragma unroll
                 for (int k = 0; k < 4; ++k) {
