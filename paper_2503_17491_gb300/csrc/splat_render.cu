@@ -493,15 +493,10 @@ __global__ void __launch_bounds__(kBlock, 3) k_render_fwd(const RenderArgs A)
                     hit = evaluate(slot_at(w, b), get_pix(w, l), A.sigma, A.alpha_min,
                                    A.alpha_max, h);
                 }
-                // this pixel's hits of the round, in list order, fetched from their lanes
+                // this pixel's hits of the round, in list order, fetched from their lanes two
+                // at a time (both fetches are issued before the first is composited)
                 uint32_t mine = lanes_keyed_to_me(hit, l, lane);
-                while (__any_sync(kFull, mine != 0u)) {
-                    const bool have = mine != 0u;
-                    const int src = have ? __ffs(mine) - 1 : lane;
-                    mine &= mine - 1u;
-                    const float a = __shfl_sync(kFull, h.a, src);
-                    const float d = __shfl_sync(kFull, h.d, src);
-                    const int bs = __shfl_sync(kFull, b, src);
+                auto blend = [&](bool have, float a, float d, int bs) {
                     if (have && !done) {
                         const float tt = __fmul_rn(T, __fsub_rn(1.0f, a));
                         if (tt < A.t_min) {
@@ -519,6 +514,22 @@ __global__ void __launch_bounds__(kBlock, 3) k_render_fwd(const RenderArgs A)
                             atomicOr(&w.hits[bs], 1u << lane);
                         }
                     }
+                };
+                while (__any_sync(kFull, mine != 0u)) {
+                    const bool have1 = mine != 0u;
+                    const int src1 = have1 ? __ffs(mine) - 1 : lane;
+                    mine &= mine - 1u;
+                    const bool have2 = mine != 0u;
+                    const int src2 = have2 ? __ffs(mine) - 1 : lane;
+                    mine &= mine - 1u;
+                    const float a1 = __shfl_sync(kFull, h.a, src1);
+                    const float d1 = __shfl_sync(kFull, h.d, src1);
+                    const int b1 = __shfl_sync(kFull, b, src1);
+                    const float a2 = __shfl_sync(kFull, h.a, src2);
+                    const float d2 = __shfl_sync(kFull, h.d, src2);
+                    const int b2 = __shfl_sync(kFull, b, src2);
+                    blend(have1, a1, d1, b1);
+                    blend(have2, a2, d2, b2);
                 }
                 if (__all_sync(kFull, done)) break;
             }
