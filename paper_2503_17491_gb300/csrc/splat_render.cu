@@ -812,6 +812,9 @@ __global__ void __launch_bounds__(kBlock, 3) k_render_bwd(const RenderArgs A)
                     for (int s = 4; s < 32; s <<= 1) {
                         const int bo = __shfl_down_sync(kFull, b, s);
                         const bool same = lane + s < 32 && bo == b;
+                        // a primitive's groups are consecutive: when none reaches s lanes ahead,
+                        // none reaches 2s ahead, and the remaining stages would add nothing
+                        if (!__any_sync(kFull, same)) break;
 #pragma unroll
                         for (int c = 0; c < 4; ++c) {
                             const float o = __shfl_down_sync(kFull, g[c], s);
