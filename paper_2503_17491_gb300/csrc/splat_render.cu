@@ -705,6 +705,14 @@ __global__ void __launch_bounds__(kBlock, 3) k_render_bwd(const RenderArgs A)
                 const uint32_t e = t < 4 * nb.K ? w.cand[t] : (31u << 5);
                 const bool valid = (e & kCandValid) != 0u;
                 const int b = (e >> 5) & 31, l = e & 31;
+                // the pixel's channel gradients meet the hit's channels in its own lane:
+                // X_k = sum_ch g_ch x_ch,k (x = d, 1, n); fetched before the evaluation so that
+                // the exchanges overlap it
+                const float gDl = __shfl_sync(kFull, gD, l);
+                const float gOl = __shfl_sync(kFull, gO, l);
+                const float gNl0 = __shfl_sync(kFull, gN0, l);
+                const float gNl1 = __shfl_sync(kFull, gN1, l);
+                const float gNl2 = __shfl_sync(kFull, gN2, l);
                 Hit h;
                 h.a = h.d = 0.0f;
                 h.clamped = false;
@@ -714,13 +722,6 @@ __global__ void __launch_bounds__(kBlock, 3) k_render_bwd(const RenderArgs A)
                     hit = evaluate(slot_at(w, b), get_pix(w, l), A.sigma, A.alpha_min,
                                    A.alpha_max, h);
                 }
-                // the pixel's channel gradients meet the hit's channels in its own lane:
-                // X_k = sum_ch g_ch x_ch,k (x = d, 1, n)
-                const float gDl = __shfl_sync(kFull, gD, l);
-                const float gOl = __shfl_sync(kFull, gO, l);
-                const float gNl0 = __shfl_sync(kFull, gN0, l);
-                const float gNl1 = __shfl_sync(kFull, gN1, l);
-                const float gNl2 = __shfl_sync(kFull, gN2, l);
                 float X = 0.0f, inv_om = 0.0f;
                 if (hit) {
                     const float4 nn = w.n[b];
