@@ -16,6 +16,11 @@
 // so the intersection math runs on all 32 lanes whatever the primitives' footprints.
 // Each pixel's lane then composites that round's hits on it in list order (front to back in the
 // forward, back to front in the backward), fetching them from the candidate lanes by shuffle.
+// The forward has a second schedule for batches whose candidates spread evenly over the block's
+// pixels: every lane takes its own pixel's candidates (a 32 x 32 bit transpose of the staged
+// primitives' pixel masks) and evaluates and blends them one per step in its registers, with no
+// hand-over; each batch takes whichever schedule its candidate counts make cheaper.  Both blend
+// every pixel's hits in list order with the same operations, so the choice changes no result.
 // A warp leaves its block as soon as all its pixels are saturated.
 //
 // Numerics.  Each pixel ray is intersected with a splat as two planes h_x, h_y through the
@@ -62,6 +67,12 @@ constexpr int kWarps = kBlock / 32;  // warps per CTA (independent)
 constexpr int kBlocksPerTile = kBlock / 32;
 constexpr int kAcc = 13;             // per staged primitive: g_ba'(3) g_bb'(3) g_c'(3) g_n(3) g_o
 constexpr uint32_t kFull = 0xFFFFFFFFu;
+// Relative cost of the forward's two schedules of a staged batch (measured on the 12-keyframe
+// render): one pixel-parallel step (every lane evaluates and blends one candidate of its own
+// pixel) against one pair-parallel round (32 candidates, then the hand-over of the hits to their
+// pixels' lanes); the batch takes the pixel-parallel schedule when
+// max_pixel_candidates * kPixelStepCost <= rounds * kRoundCost.
+constexpr int kPixelStepCost = 9, kRoundCost = 20;
 
 // A staged primitive, as four float4 rows and one float (structure of arrays, so that lanes
 // reading different primitives spread over the banks):
@@ -158,6 +169,24 @@ __device__ __forceinline__ int warp_incl_scan(int v, int lane)
         if (lane >= o) v += u;
     }
     return v;
+}
+
+// 32 x 32 bit transpose over the warp: lane j holds row j (bit l = column l); afterwards lane l
+// holds column l (bit j = bit l of row j).  Five butterfly stages each swap the off-diagonal
+// blocks of the level: the lane with bit s clear keeps the columns with bit s clear and takes its
+// partner's, the other lane the reverse.
+__device__ __forceinline__ uint32_t transpose32(uint32_t x, int lane)
+{
+    constexpr uint32_t kHigh[5] = {0xFFFF0000u, 0xFF00FF00u, 0xF0F0F0F0u, 0xCCCCCCCCu,
+                                   0xAAAAAAAAu};
+#pragma unroll
+    for (int k = 0; k < 5; ++k) {
+        const int s = 16 >> k;
+        const uint32_t y = __shfl_xor_sync(kFull, x, s);
+        x = (lane & s) ? ((x & kHigh[k]) | ((y & kHigh[k]) >> s))
+                       : ((x & ~kHigh[k]) | ((y & ~kHigh[k]) << s));
+    }
+    return x;
 }
 
 // Per-warp shared state: the staged batch (structure of arrays), the block's pixel frames
@@ -466,7 +495,26 @@ __global__ void __launch_bounds__(kBlock, 3) k_render_fwd(const RenderArgs A)
         uint32_t chain = kNoChunk;   // this item's last record chunk
         int fill = 0;                 // records in it
 
-        // stage queue entries [off, off + cnt) and composite them, round by round
+        // blend a hit (alpha a, range d, staged slot bs) into this pixel, front to back
+        auto blend = [&](float a, float d, int bs) {
+            const float tt = __fmul_rn(T, __fsub_rn(1.0f, a));
+            if (tt < A.t_min) {
+                done = true;
+                return;
+            }
+            const float wgt = __fmul_rn(a, T);
+            D = __fmaf_rn(wgt, d, D);
+            const float4 nn = w.n[bs];
+            N0 = __fmaf_rn(wgt, nn.x, N0);
+            N1 = __fmaf_rn(wgt, nn.y, N1);
+            N2 = __fmaf_rn(wgt, nn.z, N2);
+            O = __fadd_rn(O, wgt);
+            T = tt;
+            last = static_cast<int>(w.pos[bs]) + 1;
+            atomicOr(&w.hits[bs], 1u << lane);
+        };
+
+        // stage queue entries [off, off + cnt) and composite them in one of two schedules
         auto composite = [&](int cnt, int off) {
             uint32_t m = 0u;
             w.hits[lane] = 0u;
@@ -477,61 +525,66 @@ __global__ void __launch_bounds__(kBlock, 3) k_render_fwd(const RenderArgs A)
                 m = pixel_mask(q.rect[qi], bp.br, bp.bc);
             }
             m &= __ballot_sync(kFull, !done);
-            const Numbering nb = number_candidates(m, lane);
-            list_candidates(w.cand, m, nb.off, __popc(m), lane);
+            // this pixel's candidates: the slots whose mask holds it
+            uint32_t mine = transpose32(m, lane);
+            const int steps_px = static_cast<int>(
+                __reduce_max_sync(kFull, static_cast<unsigned>(__popc(mine))));
+            const int K = static_cast<int>(
+                __reduce_add_sync(kFull, static_cast<unsigned>(__popc(m))));
+            evals += __popc(mine);
             __syncwarp();
-            for (int r0 = 0; r0 < nb.K; r0 += 32) {
-                const int t = r0 + lane;
-                const uint32_t e = t < nb.K ? w.cand[t] : 0u;
-                const bool valid = (e & kCandValid) != 0u;
-                const int b = (e >> 5) & 31, l = e & 31;
-                Hit h;
-                h.a = h.d = 0.0f;
-                bool hit = false;
-                if (valid) {
-                    ++evals;
-                    hit = evaluate(slot_at(w, b), get_pix(w, l), A.sigma, A.alpha_min,
-                                   A.alpha_max, h);
-                }
-                // this pixel's hits of the round, in list order, fetched from their lanes two
-                // at a time (both fetches are issued before the first is composited)
-                uint32_t mine = lanes_keyed_to_me(hit, l, lane);
-                auto blend = [&](bool have, float a, float d, int bs) {
-                    if (have && !done) {
-                        const float tt = __fmul_rn(T, __fsub_rn(1.0f, a));
-                        if (tt < A.t_min) {
-                            done = true;
-                        } else {
-                            const float wgt = __fmul_rn(a, T);
-                            D = __fmaf_rn(wgt, d, D);
-                            const float4 nn = w.n[bs];
-                            N0 = __fmaf_rn(wgt, nn.x, N0);
-                            N1 = __fmaf_rn(wgt, nn.y, N1);
-                            N2 = __fmaf_rn(wgt, nn.z, N2);
-                            O = __fadd_rn(O, wgt);
-                            T = tt;
-                            last = static_cast<int>(w.pos[bs]) + 1;
-                            atomicOr(&w.hits[bs], 1u << lane);
+            if (steps_px * kPixelStepCost <= ((K + 31) >> 5) * kRoundCost) {
+                // pixel-parallel: each lane evaluates its own pixel's candidates in slot (= list)
+                // order and blends them in its registers
+                const Pix px = get_pix(w, lane);
+                while (__any_sync(kFull, mine != 0u)) {
+                    if (mine != 0u) {
+                        const int j = __ffs(mine) - 1;
+                        mine &= mine - 1u;
+                        Hit h;
+                        if (evaluate(slot_at(w, j), px, A.sigma, A.alpha_min, A.alpha_max, h)) {
+                            blend(h.a, h.d, j);
+                            if (done) mine = 0u;
                         }
                     }
-                };
-                while (__any_sync(kFull, mine != 0u)) {
-                    const bool have1 = mine != 0u;
-                    const int src1 = have1 ? __ffs(mine) - 1 : lane;
-                    mine &= mine - 1u;
-                    const bool have2 = mine != 0u;
-                    const int src2 = have2 ? __ffs(mine) - 1 : lane;
-                    mine &= mine - 1u;
-                    const float a1 = __shfl_sync(kFull, h.a, src1);
-                    const float d1 = __shfl_sync(kFull, h.d, src1);
-                    const int b1 = __shfl_sync(kFull, b, src1);
-                    const float a2 = __shfl_sync(kFull, h.a, src2);
-                    const float d2 = __shfl_sync(kFull, h.d, src2);
-                    const int b2 = __shfl_sync(kFull, b, src2);
-                    blend(have1, a1, d1, b1);
-                    blend(have2, a2, d2, b2);
                 }
-                if (__all_sync(kFull, done)) break;
+            } else {
+                // pair-parallel: one candidate per lane and round, numbered primitive-major
+                const Numbering nb = number_candidates(m, lane);
+                list_candidates(w.cand, m, nb.off, __popc(m), lane);
+                __syncwarp();
+                for (int r0 = 0; r0 < nb.K; r0 += 32) {
+                    const int t = r0 + lane;
+                    const uint32_t e = t < nb.K ? w.cand[t] : 0u;
+                    const bool valid = (e & kCandValid) != 0u;
+                    const int b = (e >> 5) & 31, l = e & 31;
+                    Hit h;
+                    h.a = h.d = 0.0f;
+                    bool hit = false;
+                    if (valid)
+                        hit = evaluate(slot_at(w, b), get_pix(w, l), A.sigma, A.alpha_min,
+                                       A.alpha_max, h);
+                    // this pixel's hits of the round, in list order, fetched from their lanes
+                    // two at a time (both fetches are issued before the first is blended)
+                    uint32_t hm = lanes_keyed_to_me(hit, l, lane);
+                    while (__any_sync(kFull, hm != 0u)) {
+                        const bool have1 = hm != 0u;
+                        const int src1 = have1 ? __ffs(hm) - 1 : lane;
+                        hm &= hm - 1u;
+                        const bool have2 = hm != 0u;
+                        const int src2 = have2 ? __ffs(hm) - 1 : lane;
+                        hm &= hm - 1u;
+                        const float a1 = __shfl_sync(kFull, h.a, src1);
+                        const float d1 = __shfl_sync(kFull, h.d, src1);
+                        const int b1 = __shfl_sync(kFull, b, src1);
+                        const float a2 = __shfl_sync(kFull, h.a, src2);
+                        const float d2 = __shfl_sync(kFull, h.d, src2);
+                        const int b2 = __shfl_sync(kFull, b, src2);
+                        if (have1 && !done) blend(a1, d1, b1);
+                        if (have2 && !done) blend(a2, d2, b2);
+                    }
+                    if (__all_sync(kFull, done)) break;
+                }
             }
             __syncwarp();
             // contributor records of the batch (slots with at least one contribution), in list
