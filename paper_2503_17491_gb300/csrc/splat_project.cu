@@ -202,7 +202,11 @@ __device__ uint32_t contract_bbox(v3 ba, v3 bb, v3 bc, float o, float alpha_min,
         const float dd = d.x * d.x + d.y * d.y;
         const float num = p.z * pd - d.z * pp;
         const float den = d.z * pd - p.z * dd;
-        if (den != 0.0f) {
+        // the quotient can round into (0, 1) only when num and den are non-zero with one sign
+        // and |num| < |den| (a quotient >= 1 rounds to >= 1): testing that first skips the
+        // division for most edges and changes no result
+        if (den != 0.0f && num != 0.0f && (num > 0.0f) == (den > 0.0f) &&
+            fabsf(num) < fabsf(den)) {
             const float lam = num / den;
             if (lam > 0.0f && lam < 1.0f) {
                 const v3 X{p.x + lam * d.x, p.y + lam * d.y, p.z + lam * d.z};
