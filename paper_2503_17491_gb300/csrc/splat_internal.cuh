@@ -170,20 +170,6 @@ enum : uint32_t { kCountMask = 0x3FFFFFFFu, kPairFlip = 1u << 30, kPairInvalid =
 // tile geometry shared by the binning and the render kernels
 // ---------------------------------------------------------------------------------------------
 
-// Cyclic tile-column range of a cyclic pixel-column range (integer arithmetic only).
-__host__ __device__ inline void tile_cols_of(int c0, int nc, int cols, int tw, int tiles_c,
-                                             int *tc0, int *ntc)
-{
-    if (nc >= cols) { *tc0 = 0; *ntc = tiles_c; return; }
-    int cl = c0 + nc - 1;
-    int a = c0 / tw;
-    int b = cl < cols ? cl / tw : tiles_c + (cl - cols) / tw;
-    int n = b - a + 1;
-    if (n >= tiles_c) { *tc0 = 0; *ntc = tiles_c; return; }
-    *tc0 = a;
-    *ntc = n;
-}
-
 // A pair's pixel rectangle and normal-flip bit in one word: r0 | flip << 15, r1, c0, nc, 16 bits
 // each (rows and columns are below 2^15)
 __host__ __device__ inline uint64_t pack_pixel_rect(const PairRec &rec)

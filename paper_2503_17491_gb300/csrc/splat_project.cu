@@ -140,7 +140,7 @@ __device__ __forceinline__ void elev_candidate(float z, float r, float &zh, floa
 // (where z / |xy| is stationary along the edge), and the pole the z axis reaches.  Returns the tile count and
 // fills the record's pixel rectangle.
 __device__ uint32_t contract_bbox(v3 ba, v3 bb, v3 bc, float o, float alpha_min, float sigma,
-                                  const ViewDesc &vd, int tile_h, int tile_w, PairRec &rec,
+                                  const ViewDesc &vd, int th_shift, int tw_shift, PairRec &rec,
                                   uint64_t &trect)
 {
     float x = o / alpha_min;
@@ -256,17 +256,33 @@ __device__ uint32_t contract_bbox(v3 ba, v3 bb, v3 bc, float o, float alpha_min,
             c0 = 0;
             nc = W;
         } else {
-            c0 = ((cf % W) + W) % W;
+            const int rem = cf % W;   // in (-W, W)
+            c0 = rem < 0 ? rem + W : rem;
         }
     }
+    // tile columns of the pixel columns c0 .. c0 + nc - 1 (mod W), wrapping past the last tile;
+    // tile sides are powers of two and every index here is non-negative, so shifts divide
     int tc0, ntc;
-    tile_cols_of(c0, nc, W, tile_w, vd.tiles_c, &tc0, &ntc);
+    if (nc >= W) {
+        tc0 = 0;
+        ntc = vd.tiles_c;
+    } else {
+        const int cl = c0 + nc - 1;
+        const int a = c0 >> tw_shift;
+        const int b = cl < W ? cl >> tw_shift : vd.tiles_c + ((cl - W) >> tw_shift);
+        tc0 = a;
+        ntc = b - a + 1;
+        if (ntc >= vd.tiles_c) {
+            tc0 = 0;
+            ntc = vd.tiles_c;
+        }
+    }
     rec.r0 = static_cast<int16_t>(r0);
     rec.r1 = static_cast<int16_t>(r1);
     rec.c0 = static_cast<int16_t>(c0);
     rec.nc = static_cast<int16_t>(nc);
-    const int ntr = r1 / tile_h - r0 / tile_h + 1;
-    trect = pack_tile_rect(r0 / tile_h, ntr, tc0, ntc);
+    const int ntr = (r1 >> th_shift) - (r0 >> th_shift) + 1;
+    trect = pack_tile_rect(r0 >> th_shift, ntr, tc0, ntc);
     return static_cast<uint32_t>(ntr * ntc);
 }
 
@@ -280,6 +296,7 @@ __global__ void __launch_bounds__(256) k_project(
 {
     const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
     if (i >= n) return;
+    const int th_shift = __ffs(tile_h) - 1, tw_shift = __ffs(tile_w) - 1;   // powers of two
     const float4 pl = pos_logit[i];
     const float4 q4 = quat[i];
     const float2 ls = log_scale[i];
@@ -342,8 +359,8 @@ __global__ void __launch_bounds__(256) k_project(
             const bool below = vd.cull_t_bot * rxy - bc.z > reach * vd.cull_l_bot;
             // C4: bounding box (views not sampled for this step take no pairs)
             if (!(clear && (above || below)) && !(active && !active[v]))
-                rec.cf |= contract_bbox(ba, bb, bc, oc, alpha_min, sigma, vd, tile_h, tile_w, rec,
-                                        tr);
+                rec.cf |= contract_bbox(ba, bb, bc, oc, alpha_min, sigma, vd, th_shift, tw_shift,
+                                        rec, tr);
         }
         recs[p] = rec;
         trect[p] = (rec.cf & kCountMask) ? tr : 0ull;
