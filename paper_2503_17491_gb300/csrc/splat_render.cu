@@ -805,7 +805,7 @@ __global__ void __launch_bounds__(kBlock, 3) k_render_bwd(const RenderArgs A)
                 __syncwarp();
                 float g[16];
 #pragma unroll
-                for (int c = 0; c < 16; ++c) g[c] = 0.0f;
+                for (int c = 0; c < kAcc; ++c) g[c] = 0.0f;
                 if (hit) {
                     const float2 gw = gwl[lane];
                     const float gAe = h.clamped ? 0.0f : gw.x, wgt = gw.y;
@@ -850,10 +850,16 @@ __global__ void __launch_bounds__(kBlock, 3) k_render_bwd(const RenderArgs A)
                 if (hm != 0u) {
 #pragma unroll
                     for (int c = 0; c < 8; ++c) {
-                        const bool up = (lane & 1) != 0;
-                        const float send = up ? g[c] : g[c + 8];
-                        const float keep = up ? g[c + 8] : g[c];
-                        g[c] = keep + __shfl_xor_sync(kFull, send, 1);
+                        if (c + 8 < kAcc) {
+                            const bool up = (lane & 1) != 0;
+                            const float send = up ? g[c] : g[c + 8];
+                            const float keep = up ? g[c + 8] : g[c];
+                            g[c] = keep + __shfl_xor_sync(kFull, send, 1);
+                        } else {
+                            // no term c + 8: the odd lane's slot stands for a term past the 13th,
+                            // whose value is never used, so both lanes take the sum of term c
+                            g[c] += __shfl_xor_sync(kFull, g[c], 1);
+                        }
                     }
 #pragma unroll
                     for (int c = 0; c < 4; ++c) {
