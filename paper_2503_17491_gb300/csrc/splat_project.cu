@@ -130,6 +130,29 @@ __device__ __forceinline__ void elev_candidate(float z, float r, float &zh, floa
     if (z * rl < zl * r) { zl = z; rl = r; }
 }
 
+// The view-independent part: the reach radius r_o, the half-side a and the octagon's cut c (in
+// units of a) of a primitive with opacity o; false when o stays below alpha_min everywhere.
+struct Octagon {
+    float a, k, c;
+};
+
+__device__ bool contract_octagon(float o, float alpha_min, float sigma, Octagon &oct)
+{
+    float x = o / alpha_min;
+    if (x < 0.999f) return false;
+    if (x < 1.0f) x = 1.0f;
+    const float ro = sqrtf(2.0f * contract_log(x)) * 1.001f + 0.002f;
+    const float a = ro < sigma ? ro : sigma;
+    const float k = (1.41421356f * ro) / a;
+    // the octagon (|u|, |w| <= 1, |u| + |w| <= k in units of a); when the diamond misses the
+    // square's corners (k >= 2) the cut c = 1 repeats each corner, and the repeated vertices give
+    // zero-length edges that add nothing
+    oct.a = a;
+    oct.k = k;
+    oct.c = k < 2.0f ? k - 1.0f : 1.0f;
+    return true;
+}
+
 // Spherical bounding box of the splat-space region where the primitive can contribute: the
 // 3-sigma box |s|_inf <= sigma intersected with the disk where o G(s) >= alpha_min, i.e.
 // |s| <= r_o = sqrt(2 ln(o / alpha_min)), bounded by |s|_inf <= a = min(sigma, r_o) and the
@@ -139,23 +162,13 @@ __device__ __forceinline__ void elev_candidate(float z, float r, float &zh, floa
 // the centre direction.  Elevation: the extreme of the vertices and each edge's interior extremum
 // (where z / |xy| is stationary along the edge), and the pole the z axis reaches.  Returns the tile count and
 // fills the record's pixel rectangle.
-__device__ uint32_t contract_bbox(v3 ba, v3 bb, v3 bc, float o, float alpha_min, float sigma,
-                                  const ViewDesc &vd, int th_shift, int tw_shift, PairRec &rec,
-                                  uint64_t &trect)
+__device__ uint32_t contract_bbox(v3 ba, v3 bb, v3 bc, const Octagon &oct, const ViewDesc &vd,
+                                  int th_shift, int tw_shift, PairRec &rec, uint64_t &trect)
 {
-    float x = o / alpha_min;
-    if (x < 0.999f) return 0u;
-    if (x < 1.0f) x = 1.0f;
-    const float ro = sqrtf(2.0f * contract_log(x)) * 1.001f + 0.002f;
-    const float a = ro < sigma ? ro : sigma;
-    const float k = (1.41421356f * ro) / a;
+    const float a = oct.a, k = oct.k, c = oct.c;
     const v3 A{a * ba.x, a * ba.y, a * ba.z};
     const v3 B{a * bb.x, a * bb.y, a * bb.z};
     const v3 C = bc;
-    // the octagon (|u|, |w| <= 1, |u| + |w| <= k in units of a); when the diamond misses the
-    // square's corners (k >= 2) the cut c = 1 repeats each corner, and the repeated vertices give
-    // zero-length edges that add nothing
-    const float c = k < 2.0f ? k - 1.0f : 1.0f;
     const float u[8] = {1.0f, 1.0f, c, -c, -1.0f, -1.0f, -c, c};
     const float w[8] = {-c, c, 1.0f, 1.0f, c, -c, -1.0f, -1.0f};
     v3 P[8];
@@ -310,6 +323,8 @@ __global__ void __launch_bounds__(256) k_project(
     ok = ok && qq > 0.0f && isfinite(qq);
     v3 ta{}, tb{}, tn{};
     float sa = 0.0f, sb = 0.0f, oc = 0.0f;
+    Octagon oct{};
+    bool reach = false;   // the opacity reaches alpha_min somewhere
     if (ok) {
         const float r = sqrtf(qq);
         w = w / r;
@@ -323,6 +338,7 @@ __global__ void __launch_bounds__(256) k_project(
         sa = contract_exp(ls.x);
         sb = contract_exp(ls.y);
         oc = 1.0f / (1.0f + contract_exp(-pl.w));
+        reach = contract_octagon(oc, alpha_min, sigma, oct);
     } else {
         atomicOr(status, SPLAT_STATUS_NONFINITE);
     }
@@ -358,9 +374,8 @@ __global__ void __launch_bounds__(256) k_project(
             const bool above = bc.z - vd.cull_t_top * rxy > reach * vd.cull_l_top;
             const bool below = vd.cull_t_bot * rxy - bc.z > reach * vd.cull_l_bot;
             // C4: bounding box (views not sampled for this step take no pairs)
-            if (!(clear && (above || below)) && !(active && !active[v]))
-                rec.cf |= contract_bbox(ba, bb, bc, oc, alpha_min, sigma, vd, th_shift, tw_shift,
-                                        rec, tr);
+            if (reach && !(clear && (above || below)) && !(active && !active[v]))
+                rec.cf |= contract_bbox(ba, bb, bc, oct, vd, th_shift, tw_shift, rec, tr);
         }
         recs[p] = rec;
         trect[p] = (rec.cf & kCountMask) ? tr : 0ull;
