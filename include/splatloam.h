@@ -374,7 +374,7 @@ SPLAT_API int splat_refine_step(splat_ctx *ctx, float *pos_logit, float *quat, f
  * device memory (for instance a process whose device memory is owned by another allocator, or
  * code that must not call cudaMalloc once it is running).  It renders one view like
  * splat_render, with no context: every workspace buffer lives in one array of the library
- * (about 8 MB), and the call allocates nothing -- no cudaMalloc, cudaFree or host heap.
+ * (about 9 MB), and the call allocates nothing -- no cudaMalloc, cudaFree or host heap.
  * The array and the kernels' code take device memory when CUDA loads the library's code on a
  * device, and keep it until the process exits.  CUDA loads that code when it is first used on
  * the device (lazy module loading is CUDA's default), so the FIRST call on each device is a

@@ -99,6 +99,7 @@ struct splat_ctx {
     float *d_tfinal = nullptr;
     int32_t *d_nlast = nullptr;
     float4 *d_wgrad = nullptr;
+    float4 *d_prim = nullptr;      // per primitive: the staged axes, normal and opacity
     float *d_pose = nullptr;        // per view (dL/drho, dL/domega) of the last backward
     uint2 *d_rec = nullptr;         // contributor records: chunks of 32 (forward -> backward)
     uint32_t *d_rec_prev = nullptr, *d_rec_head = nullptr, *d_rec_fill = nullptr;
@@ -163,6 +164,7 @@ splat::RenderArgs render_args(splat_ctx *ctx, const splat_gaussians *g)
     a.pos_logit = reinterpret_cast<const float4 *>(g->pos_logit);
     a.quat = reinterpret_cast<const float4 *>(g->quat_wxyz);
     a.log_scale = reinterpret_cast<const float2 *>(g->log_scale);
+    a.prim = ctx->d_prim;
     a.n = g->n;
     a.tiles = ctx->d_tileinfo;
     a.pixframes = ctx->d_pixframes;
@@ -226,7 +228,7 @@ int render_core(splat_ctx *ctx, const splat_gaussians *g, float *depth, float *n
                              ctx->n_views, ctx->cfg.sigma_cut, ctx->cfg.alpha_min, th, tw,
                              ctx->cfg.flip_normals,
                              ctx->d_recs, ctx->d_dkeys, ctx->d_dvals, ctx->d_trect,
-                             ctx->d_prect, cnt + 1,
+                             ctx->d_prect, ctx->d_prim, cnt + 1,
                              cnt + 4, st,
                              active));
     CK(stage_mark(1));
@@ -311,7 +313,7 @@ void free_ctx(splat_ctx *c)
 {
     void *ptrs[] = {c->d_views, c->d_frames, c->d_tile_view, c->d_recs, c->d_dkeys, c->d_dvals,
                     c->d_dkeys2, c->d_dvals2, c->d_trect, c->d_srect, c->d_prect, c->d_tkeys, c->d_tvals, c->d_tkeys2, c->d_tvals2,
-                    c->d_block_sums, c->d_hist, c->d_ranges, c->d_tfinal, c->d_nlast, c->d_wgrad,
+                    c->d_block_sums, c->d_hist, c->d_ranges, c->d_tfinal, c->d_nlast, c->d_wgrad, c->d_prim,
                     c->d_pose, c->d_rec, c->d_rec_prev, c->d_rec_head, c->d_rec_fill,
                     c->d_samp_thr, c->d_active, c->d_grow_sums,
                     c->d_img, c->d_gimg, c->d_counters, c->d_evals, c->d_pixframes,
@@ -415,6 +417,7 @@ SPLAT_API int splat_ctx_create(const splat_render_config *cfg, const splat_capac
     if (e == cudaSuccess) e = dalloc(&c->d_tfinal, P);
     if (e == cudaSuccess) e = dalloc(&c->d_nlast, P);
     if (e == cudaSuccess) e = dalloc(&c->d_wgrad, static_cast<size_t>(cap->max_gaussians) * 4);
+    if (e == cudaSuccess) e = dalloc(&c->d_prim, static_cast<size_t>(cap->max_gaussians) * 3);
     if (e == cudaSuccess) e = dalloc(&c->d_pose, static_cast<size_t>(cap->max_views) * 6);
     if (e == cudaSuccess) e = dalloc(&c->d_samp_thr, static_cast<size_t>(splat::kMaxViews));
     if (e == cudaSuccess) e = dalloc(&c->d_active, static_cast<size_t>(cap->max_views));

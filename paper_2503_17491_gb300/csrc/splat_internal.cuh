@@ -327,8 +327,8 @@ cudaError_t launch_project(const float4 *pos_logit, const float4 *quat, const fl
                            int64_t n, const ViewDesc *views, int n_views, float sigma,
                            float alpha_min, int tile_h, int tile_w, int flip_normals,
                            PairRec *recs, uint32_t *dkeys, uint32_t *dvals, uint64_t *trect,
-                           uint64_t *prect, uint32_t *status, uint32_t *n_valid, cudaStream_t st,
-                           const uint8_t *active = nullptr);
+                           uint64_t *prect, float4 *prim, uint32_t *status, uint32_t *n_valid,
+                           cudaStream_t st, const uint8_t *active = nullptr);
 
 // stable LSD radix sort of (uint32 key, uint32 value) pairs on key bits [0, bits);
 // the count is read on the device from *d_count (clamped to max_n); result lands in
@@ -439,6 +439,9 @@ struct RenderArgs {
     const float4 *pos_logit;
     const float4 *quat;
     const float2 *log_scale;
+    // per primitive, written by the projection: (s_a t_a, o), (s_b t_b, 0), (t_n, 0) -- the
+    // scaled tangent axes, the normal and the opacity in the world frame
+    const float4 *prim;
     int64_t n;                    // primitives per view (pair id = view * n + i)
     const TileInfo *tiles;        // global tile -> frame and addressing
     const PixFrame *pixframes;

@@ -50,7 +50,8 @@ constexpr size_t kOffDvals2 = align256(kOffDkeys2 + 4 * kMaxGaussians);
 constexpr size_t kOffTrect = align256(kOffDvals2 + 4 * kMaxGaussians);
 constexpr size_t kOffSrect = align256(kOffTrect + 8 * kMaxGaussians);
 constexpr size_t kOffPrect = align256(kOffSrect + 8 * kMaxGaussians);
-constexpr size_t kOffTkeys = align256(kOffPrect + 8 * kMaxGaussians);
+constexpr size_t kOffPrim = align256(kOffPrect + 8 * kMaxGaussians);
+constexpr size_t kOffTkeys = align256(kOffPrim + 3 * sizeof(float4) * kMaxGaussians);
 constexpr size_t kOffTvals = align256(kOffTkeys + 4 * kMaxPairs);
 constexpr size_t kOffTkeys2 = align256(kOffTvals + 4 * kMaxPairs);
 constexpr size_t kOffTvals2 = align256(kOffTkeys2 + 4 * kMaxPairs);
@@ -256,6 +257,7 @@ extern "C" SPLAT_API int splat_render_noalloc(const splat_gaussians *g,
     uint32_t *tvals = reinterpret_cast<uint32_t *>(base + kOffTvals);
     uint32_t *tkeys2 = reinterpret_cast<uint32_t *>(base + kOffTkeys2);
     uint32_t *tvals2 = reinterpret_cast<uint32_t *>(base + kOffTvals2);
+    float4 *prim = reinterpret_cast<float4 *>(base + kOffPrim);
     uint32_t *block_sums = reinterpret_cast<uint32_t *>(base + kOffBlockSums);
     uint32_t *hist = reinterpret_cast<uint32_t *>(base + kOffHist);
     uint2 *ranges = reinterpret_cast<uint2 *>(base + kOffRanges);
@@ -281,7 +283,7 @@ extern "C" SPLAT_API int splat_render_noalloc(const splat_gaussians *g,
                                 reinterpret_cast<const float4 *>(g->quat_wxyz),
                                 reinterpret_cast<const float2 *>(g->log_scale), n, view, 1,
                                 cfg.sigma_cut, cfg.alpha_min, th, tw, cfg.flip_normals, recs, dkeys,
-                                dvals, trect, prect, cnt + 1, cnt + 4, st));
+                                dvals, trect, prect, prim, cnt + 1, cnt + 4, st));
     uint32_t *dk, *dv;
     NA_CK(splat::radix_sort_pairs(dkeys, dvals, dkeys2, dvals2, nullptr, n, 32, hist, &dk, &dv, st,
                                   nullptr, trect, srect));
@@ -300,6 +302,7 @@ extern "C" SPLAT_API int splat_render_noalloc(const splat_gaussians *g,
     a.pos_logit = reinterpret_cast<const float4 *>(g->pos_logit);
     a.quat = reinterpret_cast<const float4 *>(g->quat_wxyz);
     a.log_scale = reinterpret_cast<const float2 *>(g->log_scale);
+    a.prim = prim;
     a.n = n;
     a.tiles = tiles;
     a.pixframes = pix;

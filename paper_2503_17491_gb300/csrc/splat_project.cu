@@ -14,7 +14,9 @@
 // over the views; each (view, primitive) record is 16 bytes, plus one 8-byte word with the
 // pair's tile rectangle that the range sort lays out in range order for the emission.  The
 // range-sort keys and pair ids are written here too, so the sort starts from this kernel's
-// output.
+// output.  Each primitive also gets the 48 bytes the compositing kernels stage for it -- its
+// scaled tangent axes, normal and opacity in the world frame -- so that they need not redo the
+// quaternion and exponentials for every (block, list entry).
 
 #include <cmath>
 
@@ -304,8 +306,9 @@ __global__ void __launch_bounds__(256) k_project(
     const float2 *__restrict__ log_scale, int64_t n, const ViewDesc *__restrict__ views,
     int n_views, float sigma, float alpha_min, int tile_h, int tile_w, int flip_normals,
     PairRec *__restrict__ recs, uint32_t *__restrict__ dkeys, uint32_t *__restrict__ dvals,
-    uint64_t *__restrict__ trect, uint64_t *__restrict__ prect, uint32_t *__restrict__ status,
-    uint32_t *__restrict__ n_valid, const uint8_t *__restrict__ active)
+    uint64_t *__restrict__ trect, uint64_t *__restrict__ prect, float4 *__restrict__ prim,
+    uint32_t *__restrict__ status, uint32_t *__restrict__ n_valid,
+    const uint8_t *__restrict__ active)
 {
     const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
     if (i >= n) return;
@@ -342,6 +345,10 @@ __global__ void __launch_bounds__(256) k_project(
     } else {
         atomicOr(status, SPLAT_STATUS_NONFINITE);
     }
+    // what the compositing kernels stage for every (block, list entry) of this primitive
+    prim[3 * i] = make_float4(sa * ta.x, sa * ta.y, sa * ta.z, oc);
+    prim[3 * i + 1] = make_float4(sb * tb.x, sb * tb.y, sb * tb.z, 0.0f);
+    prim[3 * i + 2] = make_float4(tn.x, tn.y, tn.z, 0.0f);
     const v3 mu{pl.x, pl.y, pl.z};
 
     uint32_t nv = 0;   // pairs of this primitive that touch a tile
@@ -397,14 +404,14 @@ cudaError_t launch_project(const float4 *pos_logit, const float4 *quat, const fl
                            int64_t n, const ViewDesc *views, int n_views, float sigma,
                            float alpha_min, int tile_h, int tile_w, int flip_normals,
                            PairRec *recs, uint32_t *dkeys, uint32_t *dvals, uint64_t *trect,
-                           uint64_t *prect, uint32_t *status, uint32_t *n_valid, cudaStream_t st,
-                           const uint8_t *active)
+                           uint64_t *prect, float4 *prim, uint32_t *status, uint32_t *n_valid,
+                           cudaStream_t st, const uint8_t *active)
 {
     if (n <= 0) return cudaSuccess;
     const unsigned grid = static_cast<unsigned>((n + 255) / 256);
     k_project<<<grid, 256, 0, st>>>(pos_logit, quat, log_scale, n, views, n_views, sigma,
                                     alpha_min, tile_h, tile_w, flip_normals, recs, dkeys, dvals,
-                                    trect, prect, status, n_valid, active);
+                                    trect, prect, prim, status, n_valid, active);
     return cudaGetLastError();
 }
 

@@ -262,25 +262,14 @@ __device__ __forceinline__ uint32_t stage(const RenderArgs &A, const TileInfo &t
 {
     const int64_t i = static_cast<int64_t>(p) - static_cast<int64_t>(ti.view) * A.n;
     const float4 pl = A.pos_logit[i];
-    const float4 q = A.quat[i];
-    const float2 ls = A.log_scale[i];
-    const float rn = rsqrtf(q.x * q.x + q.y * q.y + q.z * q.z + q.w * q.w);
-    const float qw = q.x * rn, x = q.y * rn, y = q.z * rn, z = q.w * rn;
-    const float ta0 = 1.0f - 2.0f * (y * y + z * z), ta1 = 2.0f * (x * y + qw * z),
-                ta2 = 2.0f * (x * z - qw * y);
-    const float tb0 = 2.0f * (x * y - qw * z), tb1 = 1.0f - 2.0f * (x * x + z * z),
-                tb2 = 2.0f * (y * z + qw * x);
-    const float tn0 = 2.0f * (x * z + qw * y), tn1 = 2.0f * (y * z - qw * x),
-                tn2 = 1.0f - 2.0f * (x * x + y * y);
-    const float sa = __expf(ls.x), sb = __expf(ls.y);
-    const float o = 1.0f / (1.0f + __expf(-pl.w));
+    const float4 ea = A.prim[3 * i], eb = A.prim[3 * i + 1], en = A.prim[3 * i + 2];
     const float *M = ti.M_hi;
-    w.a[s] = make_float4(sa * (M[0] * ta0 + M[1] * ta1 + M[2] * ta2),
-                         sa * (M[3] * ta0 + M[4] * ta1 + M[5] * ta2),
-                         sa * (M[6] * ta0 + M[7] * ta1 + M[8] * ta2), o);
-    w.b[s] = make_float4(sb * (M[0] * tb0 + M[1] * tb1 + M[2] * tb2),
-                         sb * (M[3] * tb0 + M[4] * tb1 + M[5] * tb2),
-                         sb * (M[6] * tb0 + M[7] * tb1 + M[8] * tb2), __uint_as_float(rect));
+    w.a[s] = make_float4(M[0] * ea.x + M[1] * ea.y + M[2] * ea.z,
+                         M[3] * ea.x + M[4] * ea.y + M[5] * ea.z,
+                         M[6] * ea.x + M[7] * ea.y + M[8] * ea.z, ea.w);
+    w.b[s] = make_float4(M[0] * eb.x + M[1] * eb.y + M[2] * eb.z,
+                         M[3] * eb.x + M[4] * eb.y + M[5] * eb.z,
+                         M[6] * eb.x + M[7] * eb.y + M[8] * eb.z, __uint_as_float(rect));
     f2 c[3];
 #pragma unroll
     for (int r = 0; r < 3; ++r)
@@ -291,9 +280,9 @@ __device__ __forceinline__ uint32_t stage(const RenderArgs &A, const TileInfo &t
     const float *R = ti.R;
     const float fs = flip ? -1.0f : 1.0f;
     w.c[s] = make_float4(c[0].h, c[1].h, c[2].h, c[0].l);
-    w.n[s] = make_float4(fs * (R[0] * tn0 + R[1] * tn1 + R[2] * tn2),
-                         fs * (R[3] * tn0 + R[4] * tn1 + R[5] * tn2),
-                         fs * (R[6] * tn0 + R[7] * tn1 + R[8] * tn2), c[1].l);
+    w.n[s] = make_float4(fs * (R[0] * en.x + R[1] * en.y + R[2] * en.z),
+                         fs * (R[3] * en.x + R[4] * en.y + R[5] * en.z),
+                         fs * (R[6] * en.x + R[7] * en.y + R[8] * en.z), c[1].l);
     w.czl[s] = c[2].l;
     return static_cast<uint32_t>(i);
 }
