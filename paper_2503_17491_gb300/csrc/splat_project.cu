@@ -327,7 +327,7 @@ __global__ void __launch_bounds__(256) k_project(
     v3 ta{}, tb{}, tn{};
     float sa = 0.0f, sb = 0.0f, oc = 0.0f;
     Octagon oct{};
-    bool reach = false;   // the opacity reaches alpha_min somewhere
+    bool opaque = false;   // the opacity reaches alpha_min somewhere
     if (ok) {
         const float r = sqrtf(qq);
         w = w / r;
@@ -341,7 +341,7 @@ __global__ void __launch_bounds__(256) k_project(
         sa = contract_exp(ls.x);
         sb = contract_exp(ls.y);
         oc = 1.0f / (1.0f + contract_exp(-pl.w));
-        reach = contract_octagon(oc, alpha_min, sigma, oct);
+        opaque = contract_octagon(oc, alpha_min, sigma, oct);
     } else {
         atomicOr(status, SPLAT_STATUS_NONFINITE);
     }
@@ -381,7 +381,7 @@ __global__ void __launch_bounds__(256) k_project(
             const bool above = bc.z - vd.cull_t_top * rxy > reach * vd.cull_l_top;
             const bool below = vd.cull_t_bot * rxy - bc.z > reach * vd.cull_l_bot;
             // C4: bounding box (views not sampled for this step take no pairs)
-            if (reach && !(clear && (above || below)) && !(active && !active[v]))
+            if (opaque && !(clear && (above || below)) && !(active && !active[v]))
                 rec.cf |= contract_bbox(ba, bb, bc, oct, vd, th_shift, tw_shift, rec, tr);
         }
         recs[p] = rec;

@@ -154,6 +154,32 @@ def test_workload3_lists_bit_exact(tile):
     assert check_lists(ctx, s, s.views, tile) > 10 * s.n
 
 
+@pytest.mark.parametrize("tile", [(16, 16), (8, 32)])
+def test_primitives_below_alpha_min_take_no_tiles(tile):
+    """Primitives whose opacity stays below alpha_min everywhere (o < 0.999 alpha_min, Sec. 3.2.3
+    reading) reach no pixel and take no tile: among them the empty slots the map growth writes
+    (world origin, unit scale, logit -30, here at the sensor itself) and opacities on both sides
+    of the threshold.  Lists bit-exact against the oracle, images within tolerance."""
+    s = scenes.workload(0)
+    i = np.arange(s.n)
+    amin = 1.0 / 255.0
+    s.pos_logit[i % 7 == 0, 3] = -30.0
+    empty = i % 7 == 1
+    s.pos_logit[empty] = (0.0, 0.0, 0.0, -30.0)
+    s.quat[empty] = (1.0, 0.0, 0.0, 0.0)
+    s.log_scale[empty] = 0.0
+    for k, f in ((2, 0.9985), (3, 0.995), (4, 1.0005)):
+        o = f * amin
+        s.pos_logit[i % 11 == k, 3] = math.log(o / (1.0 - o))
+    ctx, d, n, a = _render(s, s.views, tile)
+    assert ctx.status() == 0
+    check_lists(ctx, s, s.views, tile)
+    rec = ctx.pair_records(s.n)
+    assert (rec["count"][(i % 7 <= 1) | (i % 11 == 3)] == 0).all()
+    ref, *_ = oracle_view(s, s.views[0], tile)
+    compare_images(d, n, a, ref, f"below alpha_min {tile}")
+
+
 def test_empty_and_single():
     v = scenes.View(np.eye(4), 16, 64, scenes.deg(-10), scenes.deg(10))
     ctx = make_ctx(4, [v])
