@@ -212,7 +212,8 @@ SPLAT_API int splat_render_views(splat_ctx *ctx, const splat_gaussians *g, float
  * pass (Supp. D.2) replays, for each pixel, exactly the contributions the forward composited (the
  * forward records them per 4 x 8 pixel block in the context's workspace), recovers the
  * transmittance by division and sums each primitive's per-pixel terms before one set of atomics
- * per (block, primitive).
+ * per (block, primitive).  g must hold the parameters of that render: the replay stages the
+ * primitives the render's projection prepared, and the chain rule is taken at g.
  * Errors: INVALID_ARG, STATE (no render before), CUDA. */
 SPLAT_API int splat_render_views_backward(splat_ctx *ctx, const splat_gaussians *g,
                                           const float *dL_ddepth, const float *dL_dnormal,
