@@ -47,8 +47,10 @@
 // contributed to (contributor records, below); the backward walks those records back to front, so
 // it evaluates exactly the forward's contributing pairs and no others.  The backward recovers
 // T_k = T_{k+1} / (1 - alpha_k) from the final transmittance and keeps the suffix sums B_{d,k},
-// B_{n,k}, B_{o,k} of Supp. D.2 in the pixel's lane; the pixel lane hands dL/dalpha_k and the
-// blending weight back to the candidate lane, which forms the pair's 13 geometric terms.  The
+// B_{n,k}, B_{o,k} of Supp. D.2 (as one sum over the channels) in the pixel's lane.  Within a
+// round every hit is an affine map of the pixel's (T, sum) state, so each hit lane composes the
+// maps of the pixel's earlier hits of the round by pointer jumping, reads the pixel's state once,
+// and forms its own dL/dalpha_k and blending weight and the pair's 13 geometric terms.  The
 // backward numbers candidates in groups of four lanes that share one primitive (a primitive's
 // pixels fill whole groups), so the terms are summed inside the group by two exchanges, then
 // across the consecutive groups of one primitive by a segmented suffix sum, and the primitive's
@@ -770,34 +772,52 @@ __global__ void __launch_bounds__(kBlock, 3) k_render_bwd(const RenderArgs A)
                     X = gDl * h.d + gOl + gNl0 * nn.x + gNl1 * nn.y + gNl2 * nn.z;
                     inv_om = __fdividef(1.0f, __fsub_rn(1.0f, h.a));
                 }
-                // each pixel lane walks its hits of the round back to front: T_k = T_{k+1} /
-                // (1 - alpha_k) and dL/dalpha_k = T_k X_k - Y / (1 - alpha_k), with
-                // Y = sum_ch g_ch B_ch,k kept as one suffix sum (Y += w_k X_k), handing
-                // dL/dalpha_k and the weight back to the hit's lane
-                uint32_t mine = lanes_keyed_to_me(hit, l, lane);
-                while (__any_sync(kFull, mine != 0u)) {
-                    const bool have = mine != 0u;
-                    const int src = have ? __ffs(mine) - 1 : lane;
-                    mine &= mine - 1u;
-                    const float a = __shfl_sync(kFull, h.a, src);
-                    const float xk = __shfl_sync(kFull, X, src);
-                    const float io = __shfl_sync(kFull, inv_om, src);
-                    if (have) {
-                        const float Tk = T * io;
-                        const float wgt = __fmul_rn(a, Tk);
-                        const float gA = Tk * xk - Y * io;
-                        Y += wgt * xk;
-                        T = Tk;
-                        gwl[src] = make_float2(gA, wgt);
+                // The round's hits on a pixel, back to front in lane order: hit k takes the
+                // pixel's (T, Y) -- transmittance and Y = sum_ch g_ch B_ch,k, the suffix sum of
+                // Supp. D.2 -- to (T io_k, Y + a_k X_k io_k T), io_k = 1 / (1 - alpha_k): an
+                // affine map (s_k, c_k) = (io_k, a_k X_k io_k).  Each hit lane composes the maps
+                // of the pixel's earlier hits by pointer jumping along the chain of the pixel's
+                // hit lanes, applies them to the pixel's state at the round start, and forms
+                // T_k = T io_k, w_k = alpha_k T_k and dL/dalpha_k = T_k X_k - Y io_k itself; the
+                // pixel lane then applies the composition of all its hits of the round.
+                const uint32_t mine = lanes_keyed_to_me(hit, l, lane);   // pixel lane: its hits
+                const uint32_t peers = __shfl_sync(kFull, mine, l);      // hit lane: its pixel's
+                const int prev0 = hit ? 31 - __clz(peers & ((1u << lane) - 1u)) : -1;
+                float ms = hit ? inv_om : 1.0f, mc = hit ? h.a * X * inv_om : 0.0f;
+                int pv = prev0;
+                while (__any_sync(kFull, pv >= 0)) {
+                    const int src = pv >= 0 ? pv : lane;
+                    const float ps = __shfl_sync(kFull, ms, src);
+                    const float pc = __shfl_sync(kFull, mc, src);
+                    const int pp = __shfl_sync(kFull, pv, src);
+                    if (pv >= 0) {
+                        mc = pc + ps * mc;
+                        ms = ps * ms;
+                        pv = pp;
                     }
                 }
-                __syncwarp();
+                const int xsrc = prev0 >= 0 ? prev0 : lane;   // the earlier hits' composition
+                const float xs0 = __shfl_sync(kFull, ms, xsrc);
+                const float xc0 = __shfl_sync(kFull, mc, xsrc);
+                const float xs = prev0 >= 0 ? xs0 : 1.0f, xc = prev0 >= 0 ? xc0 : 0.0f;
+                const float Tl = __shfl_sync(kFull, T, l), Yl = __shfl_sync(kFull, Y, l);
+                {
+                    const int last = mine != 0u ? 31 - __clz(mine) : lane;
+                    const float ls = __shfl_sync(kFull, ms, last);
+                    const float lc = __shfl_sync(kFull, mc, last);
+                    if (mine != 0u) {
+                        Y = Y + lc * T;
+                        T = ls * T;
+                    }
+                }
                 float g[16];
 #pragma unroll
                 for (int c = 0; c < kAcc; ++c) g[c] = 0.0f;
                 if (hit) {
-                    const float2 gw = gwl[lane];
-                    const float gAe = h.clamped ? 0.0f : gw.x, wgt = gw.y;
+                    const float Tp = xs * Tl, Yp = Yl + xc * Tl;
+                    const float Tk = Tp * inv_om;
+                    const float wgt = __fmul_rn(h.a, Tk);
+                    const float gAe = h.clamped ? 0.0f : Tk * X - Yp * inv_om;
                     const SlotRef st = slot_at(w, b);
                     const Pix px = get_pix(w, l);
                     const float gd = gDl * wgt;            // dL/dd_k
