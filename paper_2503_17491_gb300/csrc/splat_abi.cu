@@ -162,8 +162,6 @@ splat::RenderArgs render_args(splat_ctx *ctx, const splat_gaussians *g)
 {
     splat::RenderArgs a{};
     a.pos_logit = reinterpret_cast<const float4 *>(g->pos_logit);
-    a.quat = reinterpret_cast<const float4 *>(g->quat_wxyz);
-    a.log_scale = reinterpret_cast<const float2 *>(g->log_scale);
     a.prim = ctx->d_prim;
     a.n = g->n;
     a.tiles = ctx->d_tileinfo;

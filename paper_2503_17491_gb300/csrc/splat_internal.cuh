@@ -436,9 +436,7 @@ cudaError_t launch_order_tiles(const uint2 *ranges, int64_t n_tiles, uint32_t *o
                                cudaStream_t st);
 
 struct RenderArgs {
-    const float4 *pos_logit;
-    const float4 *quat;
-    const float2 *log_scale;
+    const float4 *pos_logit;      // per primitive: centre (the opacity logit is not read)
     // per primitive, written by the projection: (s_a t_a, o), (s_b t_b, 0), (t_n, 0) -- the
     // scaled tangent axes, the normal and the opacity in the world frame
     const float4 *prim;

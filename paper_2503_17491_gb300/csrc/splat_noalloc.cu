@@ -300,8 +300,6 @@ extern "C" SPLAT_API int splat_render_noalloc(const splat_gaussians *g,
 
     splat::RenderArgs a{};
     a.pos_logit = reinterpret_cast<const float4 *>(g->pos_logit);
-    a.quat = reinterpret_cast<const float4 *>(g->quat_wxyz);
-    a.log_scale = reinterpret_cast<const float2 *>(g->log_scale);
     a.prim = prim;
     a.n = n;
     a.tiles = tiles;

@@ -690,7 +690,7 @@ __global__ void __launch_bounds__(kBlock, 3) k_render_fwd(const RenderArgs A)
 struct BwdShared {
     WarpBatch w[kWarps];
     float acc[kWarps][32][kAcc];
-    float2 gw[kWarps][32];   // per candidate lane: (dL/dalpha, blending weight) from its pixel
+    float pose[kWarps][16];  // the batch's reduced sensor-pose terms (9 used)
     TileInfo ti[kWarps];
 };
 
@@ -703,7 +703,7 @@ __global__ void __launch_bounds__(kBlock, 3) k_render_bwd(const RenderArgs A)
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     WarpBatch &w = sh.w[warp];
     float(*acc)[kAcc] = sh.acc[warp];
-    float2 *gwl = sh.gw[warp];
+    float *pose_sums = sh.pose[warp];
     TileInfo &ti = sh.ti[warp];
     unsigned long long evals = 0;
 
@@ -972,7 +972,7 @@ __global__ void __launch_bounds__(kBlock, 3) k_render_bwd(const RenderArgs A)
                 const float tot = v[0] + __shfl_xor_sync(kFull, v[0], 16);
                 const int idx = ((lane & 1) ? 8 : 0) + ((lane & 2) ? 4 : 0) +
                                 ((lane & 4) ? 2 : 0) + ((lane & 8) ? 1 : 0);
-                float *scratch = reinterpret_cast<float *>(gwl);
+                float *scratch = pose_sums;
                 if (lane < 16 && idx < 9) scratch[idx] = tot;
                 __syncwarp();
                 if (lane < 6) {
