@@ -587,16 +587,15 @@ def run_mapping(args):
     t0 = time.perf_counter()
     targets = _raycast_scans(scene, idx)
     t_cast = time.perf_counter() - t0
-    tile = (8, 32) if args.tile == "auto" else tuple(int(x) for x in args.tile.split("x"))
-    cfg = api.RenderConfig(tile_h=tile[0], tile_w=tile[1])
     P1 = 128 * 1024
     dev_targets = [(torch.from_numpy(d).to(dev), torch.from_numpy(n).to(dev)) for d, n in targets]
     host_targets = [(torch.from_numpy(d).pin_memory(), torch.from_numpy(n).pin_memory())
                     for d, n in targets]
     flush_buf = torch.empty(256 << 20, dtype=torch.float32, device=dev)
 
-    def mapper():
-        return api.Mapper(n_total, window, window * P1, n_new, cfg=cfg, draws=0,
+    def mapper(shape):
+        c = api.RenderConfig(tile_h=shape[0], tile_w=shape[1])
+        return api.Mapper(n_total, window, window * P1, n_new, cfg=c, draws=0,
                           max_keyframes=window, device=dev)
 
     def scan(m, j, e2e):
@@ -611,8 +610,30 @@ def run_mapping(args):
             return m.loss_out.to("cpu", non_blocking=True)
         return None
 
+    # tile shape: with --tile auto, the whole run once per shape (untimed, host clock around a
+    # synchronised run), the fastest kept -- the map's horizon tiles hold the longest lists, and
+    # their length depends on the shape
+    autotune = None
+    if args.tile == "auto":
+        autotune = {}
+        for shape in ((16, 16), (8, 32), (32, 8), (4, 64)):
+            pm = mapper(shape)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            for j in range(len(idx)):
+                scan(pm, j, False)
+            torch.cuda.synchronize()
+            autotune[f"{shape[0]}x{shape[1]}"] = max_over_ranks(
+                dist, (time.perf_counter() - t0) * 1e3, dev)
+            pm.ctx.close()
+            del pm
+        tile = min(((16, 16), (8, 32), (32, 8), (4, 64)),
+                   key=lambda sh: autotune[f"{sh[0]}x{sh[1]}"])
+    else:
+        tile = tuple(int(x) for x in args.tile.split("x"))
+
     # warm-up: a few scans of a throwaway run
-    wm = mapper()
+    wm = mapper(tile)
     for j in range(min(max(args.warmup, 1), len(idx))):
         scan(wm, j, False)
     torch.cuda.synchronize()
@@ -620,7 +641,7 @@ def run_mapping(args):
     del wm
 
     def timed_run(e2e):
-        m = mapper()
+        m = mapper(tile)
         ms, px = [], []
         barrier(dist)
         torch.cuda.synchronize()
@@ -729,6 +750,7 @@ def run_mapping(args):
         "gpu_launches": st["kernel_launches"],
         "clocks": clocks,
         "status": status,
+        "autotune": autotune,
     }
 
 
